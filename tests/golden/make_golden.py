@@ -1,0 +1,43 @@
+"""Writes the stored expected values under tests/golden/ by running the CPU oracle only.
+
+    python tests/golden/make_golden.py
+
+Each file records the seeded workload it came from and the oracle's nev smallest
+eigenvalues (Algorithm 1 run to tol = 1e-12 on ||A x - lambda x||, ||x|| = 1), so that
+GPU parity tests at full size need not rerun the (slow) oracle.  Nothing here touches
+the CUDA library.
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import jsym  # noqa: E402
+from oracle import trlan_jsym as tj  # noqa: E402
+from paper_2001_07428_gb300 import inputs  # noqa: E402
+
+
+def stencil_golden(name, tol=1e-12):
+    w = inputs.WORKLOADS[name]
+    dims = w["dims"]
+    U, W = inputs.stencil_links(dims, w["seed"])
+    n = 6 * inputs.lattice_volume(dims)
+    mv = lambda x: jsym.stencil_matvec(U, W, dims, w["m0"], w["kappa"], x)
+    t0 = time.time()
+    out = tj.trlan_jsym(mv, n, w["nev"], w["m"], w["mwin"], tol)
+    rec = dict(workload=name, params=dict(w, dims=list(dims)), tol=tol,
+               evals=[float(v) for v in out["evals"]], res=[float(v) for v in out["res"]],
+               n_matvec=out["n_matvec"], n_restarts=out["n_restarts"],
+               oracle_seconds=round(time.time() - t0, 1))
+    with open(os.path.join(HERE, f"{name}.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(name, rec["n_matvec"], rec["n_restarts"], rec["oracle_seconds"])
+
+
+if __name__ == "__main__":
+    stencil_golden("stencil_8x8x8x8")
