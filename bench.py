@@ -1,0 +1,357 @@
+"""Benchmark: time to nev converged eigenpairs (J-TRLan, residual <= 1e-8) on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
+
+One "step" is one full TRLAN-JSYM solve (Algorithm 1 with the Lanczos step of Algorithm 2) of the
+seeded synthetic workload, operator already resident in HBM.  Prints one JSON line (rank 0).
+
+* value: mean device time per solve over the K timed steps (CUDA events on the library stream;
+  L2 flushed by a 512 MB write before every step, outside the timed events), max over ranks.
+* e2e: the same solve through the C ABI from pinned HOST buffers -- jtrlan_create (H2D of the
+  operator), jtrlan_solve, jtrlan_pairs into host memory (D2H of the eigenvectors), destroy.
+* roofline: the kernel class with the largest device time in one extra profiled solve
+  (per-launch CUDA events inside the library), algorithmic work / its summed time.
+* cpu_baseline: the CPU FP64 oracle (single thread), timed on a bounded sample of the same solve.
+* --impl reference: the oracle itself is the reference arm (there is no reference code).
+Under torchrun with N > 1 every rank solves its own replica (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2001_07428_gb300 import inputs  # noqa: E402
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+TOL = 1e-8
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max clock
+L2_FLUSH_BYTES = 512 << 20
+
+# Algorithmic cost per unit of work (see the library's jtrlan_profile documentation).
+#   matvec / resid: per lattice site, 32 complex 3x3 matrix-vector products (9 complex FMA each,
+#     8 flop) = 2304 flop; bytes = 84 complex words (72 link + 6 in + 6 out) x 16 B (c128).
+#   gs_first / gs_dot / gs_update: per row pair x column, 4 complex FMA = 32 flop; bytes = the two
+#     complex128 basis entries read = 32 B.
+#   rotate: per real multiply-add 2 flop; bytes negligible per unit (V read once, counted apart).
+FLOP_PER_UNIT = {"matvec": 2304.0, "resid": 2304.0, "gs_first": 32.0, "gs_dot": 32.0, "gs_update": 32.0,
+                 "rotate": 1.0}
+BYTES_PER_UNIT = {"matvec": 84 * 16.0, "resid": 84 * 16.0, "gs_first": 32.0, "gs_dot": 32.0,
+                  "gs_update": 32.0}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload(name):
+    w = dict(inputs.WORKLOADS[name])
+    if w["kind"] != "stencil":
+        raise SystemExit("bench.py times the stencil workloads")
+    return w
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+class Clocks:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"jtrlan_clocks_{os.getpid()}.csv")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(name, restarts):
+    """Runs the oracle's Algorithm 1 for `restarts` outer iterations; returns (seconds, restarts done)."""
+    from oracle import jsym
+    from oracle import trlan_jsym as tj
+    w = workload(name)
+    dims = w["dims"]
+    U, W = inputs.stencil_links(dims, w["seed"])
+    n = 6 * inputs.lattice_volume(dims)
+    mv = lambda x: jsym.stencil_matvec(U, W, dims, w["m0"], w["kappa"], x)
+    t0 = time.perf_counter()
+    done = restarts
+    try:
+        out = tj.trlan_jsym(mv, n, w["nev"], w["m"], w["mwin"], TOL, max_restarts=restarts)
+        done = out["n_restarts"]
+    except tj.NoConvergenceError:
+        pass
+    return time.perf_counter() - t0, done
+
+
+def cpu_baseline(name, full_restarts, restarts=4):
+    """The oracle timed single-threaded in a child process (BLAS pinned to one thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", name, "--sample-restarts", str(restarts)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        return {"value": None, "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    value = d["seconds"] * full_restarts / d["restarts"]
+    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"first {d['restarts']} of {full_restarts} outer iterations of the same solve "
+                      f"({d['seconds']:.1f} s), scaled by outer-iteration count"}
+
+
+# ---------------------------------------------------------------- the reference arm (the oracle)
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    g = os.path.join(GOLDEN, f"{args.workload}.json")
+    full = json.load(open(g)).get("tol_1e-8", {}).get("n_restarts") if os.path.exists(g) else None
+    full = full or 30
+    restarts = 3
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are skipped
+    times = []
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    for _ in range(args.steps):
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", args.workload,
+               "--sample-restarts", str(restarts)]
+        r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        times.append(d["seconds"] * full / d["restarts"])
+    value = statistics.mean(times)
+    line = {"impl": "reference", "metric": metric_name(w), "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args.workload, w),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: first {restarts} of {full} outer iterations, scaled"},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def metric_name(w):
+    return (f"time to {w['nev']} eigenpairs at resid<=1e-8 (J-TRLan, plain FP64)")
+
+
+def config_of(name, w):
+    return {"workload": name, "n": 6 * inputs.lattice_volume(w["dims"]), "lattice": list(w["dims"]),
+            "nev": w["nev"], "m": w["m"], "mwin": w["mwin"], "tol": TOL, "m0": w["m0"], "kappa": w["kappa"],
+            "precision": "fp64", "inputs": "seeded Haar SU(3) U, complex Gaussian W",
+            "l2": "flushed before every timed step (512 MB write)"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_gb300(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2001_07428_gb300 import binding as B
+
+    B.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    dims = w["dims"]
+    U, W = inputs.stencil_links(dims, w["seed"])
+    n = 6 * inputs.lattice_volume(dims)
+    Ud = torch.from_numpy(U).to(dev)
+    Wd = torch.from_numpy(W).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    op = B.stencil_operator(dims, w["m0"], w["kappa"], Ud.data_ptr(), Wd.data_ptr())
+    prm = B.params(w["nev"], w["m"], w["mwin"], TOL)
+    ctx = B.jtrlan_create(op, prm, stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        st = B.jtrlan_solve(ctx)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    stats = []
+    clocks = Clocks(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev0[i].record(stream)
+        st = B.jtrlan_solve(ctx)
+        ev1[i].record(stream)
+        launches += st["n_launches"]
+        stats.append(st)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) / 1e3 for a, b in zip(ev0, ev1)]
+    t_mean = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([t_mean], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_mean = float(t.item())
+
+    # ---- one profiled solve: per-kernel device time
+    prm_p = B.params(w["nev"], w["m"], w["mwin"], TOL, profile=1)
+    ctxp = B.jtrlan_create(op, prm_p, stream.cuda_stream)
+    flush.zero_()
+    torch.cuda.synchronize()
+    stp = B.jtrlan_solve(ctxp)
+    prof = B.jtrlan_get_profile(ctxp)
+    B.jtrlan_destroy(ctxp)
+    tot_ms = sum(v["ms"] for v in prof.values())
+    kernels = {}
+    for k, v in prof.items():
+        if v["launches"] == 0:
+            continue
+        e = {"ms": round(v["ms"], 3), "launches": v["launches"], "share": round(v["ms"] / tot_ms, 4)}
+        if k in FLOP_PER_UNIT and v["ms"] > 0:
+            e["tflops"] = round(v["work"] * FLOP_PER_UNIT[k] / (v["ms"] * 1e-3) / 1e12, 4)
+        if k in BYTES_PER_UNIT and v["ms"] > 0:
+            e["gbs"] = round(v["work"] * BYTES_PER_UNIT[k] / (v["ms"] * 1e-3) / 1e9, 1)
+        kernels[k] = e
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    hbm_peak, hbm_src = measured_peaks()
+    if "tflops" in kernels[dom]:
+        ach = kernels[dom]["tflops"]
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": round(FP64_PEAK_TFLOPS, 3),
+                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    else:
+        roof = {"kernel": dom, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    mvk = kernels.get("matvec", {})
+    stencil = {"gbs": mvk.get("gbs"), "frac_of_hbm": round(mvk["gbs"] / hbm_peak, 4) if mvk.get("gbs") else None,
+               "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src, "tflops": mvk.get("tflops"),
+               "frac_of_fp64": round(mvk["tflops"] / FP64_PEAK_TFLOPS, 4) if mvk.get("tflops") else None,
+               "note": "8^4 in c128 is L2-resident (5.5 MB) and FP64-ALU-bound; GB/s counts 84 words/site"}
+
+    # ---- end to end through the C ABI from pinned host buffers
+    Uh = torch.from_numpy(U).pin_memory()
+    Wh = torch.from_numpy(W).pin_memory()
+    Xh = torch.empty((w["nev"], n), dtype=torch.complex128).pin_memory()
+    evh = np.zeros(w["nev"])
+    resh = np.zeros(w["nev"])
+    op_h = B.stencil_operator(dims, w["m0"], w["kappa"], Uh.data_ptr(), Wh.data_ptr())
+    import ctypes
+    e2e = []
+    torch.cuda.synchronize()
+    for i in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = B.jtrlan_create(op_h, prm, stream.cuda_stream)
+        B.jtrlan_solve(c2)
+        B.jtrlan_pairs(c2, 0, evh.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(Xh.data_ptr()),
+                       resh.ctypes.data_as(ctypes.c_void_p))
+        B.jtrlan_destroy(c2)
+        e2e.append(time.perf_counter() - t0)
+    e2e_mean = statistics.mean(e2e)
+    if world > 1:
+        t = torch.tensor([e2e_mean], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_mean = float(t.item())
+    h2d = Uh.numel() * 16 + Wh.numel() * 16
+    d2h = Xh.numel() * 16 + 2 * w["nev"] * 8
+    B.jtrlan_destroy(ctx)
+
+    if rank != 0:
+        return
+    line = {"metric": metric_name(w), "value": t_mean, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_mean * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args.workload, w),
+            "solve_stats": {k: stats[-1][k] for k in ("n_matvec", "n_resid_matvec", "n_gs_passes", "n_restarts",
+                                                       "icnv")},
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "stencil_matvec": stencil,
+            "kernels": kernels,
+            "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, stats[-1]["n_restarts"])
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="stencil_8x8x8x8")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--sample-restarts", type=int, default=4, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        sec, done = oracle_sample(args.oracle_sample, args.sample_restarts)
+        print(json.dumps({"seconds": sec, "restarts": done}))
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_gb300(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

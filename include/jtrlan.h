@@ -1,0 +1,184 @@
+/* jtrlan.h -- C ABI of libjtrlan: thick-restart Lanczos for Hermitian J-symmetric matrices
+ * (TRLAN-JSYM) on one NVIDIA GB300 (sm_103a).
+ *
+ * Paper: T. Ishikawa and T. Sogabe, "A thick-restart Lanczos type method for Hermitian
+ * J-symmetric eigenvalue problems" (arXiv:2001.07428).
+ *
+ * Problem (Sec. 1, eqs. (1), (2), (4)): A is Hermitian and J-symmetric, J A J^{-1} = A^T with
+ * the canonical J = [[O, -I], [I, O]], so A = [[A11, A12], [A12^H, A11^T]] with A11^H = A11 and
+ * A12^T = -A12.  Every eigenvalue is doubly degenerate and y = J x* pairs each eigenvector x
+ * with a second one.  Algorithm 1 (TRLAN-JSYM) with the Lanczos step of Algorithm 2 finds the
+ * nev wanted eigenvalues once each, searching only one of the two orthogonal half-spaces.
+ *
+ * Vector layout (canonical): n complex numbers, x = [x1; x2], each half n/2 long.  Complex
+ * numbers are stored as interleaved (re, im) pairs: double2 for JTRLAN_C128, float2 for
+ * JTRLAN_C64.  Matrices of vectors (eigenvectors) are column-major, one vector per column.
+ *
+ * Conventions for every call:
+ *   - Every call returns a jtrlan_status and never throws or aborts across the ABI.
+ *   - All GPU work is enqueued on the CUDA stream given to jtrlan_create (NULL = legacy
+ *     default stream).  Calls that return host data synchronise that stream.
+ *   - Pointers documented as "host or device" may be either: copies use unified addressing.
+ *   - jtrlan_last_error() returns a thread-local text for the last failing call.
+ */
+#ifndef JTRLAN_H
+#define JTRLAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  JTRLAN_OK = 0,
+  JTRLAN_EINVAL = 1,      /* invalid argument (sizes, parameters, null pointer) */
+  JTRLAN_ENOMEM = 2,      /* device or host allocation failed */
+  JTRLAN_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  JTRLAN_ENOTJSYM = 4,    /* the Lemma 1 self-check found the operator not J-symmetric */
+  JTRLAN_EBREAKDOWN = 5,  /* Lanczos breakdown: beta below the breakdown threshold */
+  JTRLAN_ENOCONV = 6,     /* max_restarts reached before nev pairs converged */
+  JTRLAN_ETIMEOUT = 7,    /* reserved: a bounded device-side wait ran out */
+  JTRLAN_ESTATE = 8       /* call out of order (e.g. pairs before a successful solve) */
+} jtrlan_status;
+
+enum { JTRLAN_DENSE = 0, JTRLAN_STENCIL4D = 1 };     /* jtrlan_operator.kind   */
+enum { JTRLAN_C128 = 0, JTRLAN_C64 = 1 };            /* jtrlan_operator.dtype  */
+enum { JTRLAN_SMALLEST = 0, JTRLAN_LARGEST = 1 };    /* jtrlan_params.which    */
+enum { JTRLAN_FP64 = 0, JTRLAN_MIXED = 1 };          /* jtrlan_params.precision */
+
+/* The operator A in the block form of eq. (4).
+ *
+ * kind = JTRLAN_DENSE: a11 and a12 are (n/2) x (n/2) row-major complex matrices (host or
+ *   device), the blocks A11 (Hermitian) and A12 (skew-symmetric) of eq. (4).  Only these two
+ *   blocks are read; A12^H and A11^T are applied through conjugation.
+ * kind = JTRLAN_STENCIL4D: a periodic 4D lattice dims[0..3] = (Lx, Ly, Lz, Lt) with site index
+ *   s = x + Lx*(y + Ly*(z + Lz*t)), three colours per site, n = 6 * Lx*Ly*Lz*Lt.  U and W are
+ *   link fields of shape [4][V][3][3] row-major complex (host or device), direction mu = 0..3
+ *   along x, y, z, t.  The blocks are
+ *     (A11 p)(s) = m0 p(s) + sum_mu [U_mu(s) p(s+mu) + U_mu(s-mu)^H p(s-mu)],
+ *     (A12 p)(s) = kappa * sum_mu [W_mu(s) p(s+mu) - W_mu(s-mu)^T p(s-mu)],
+ *   which are Hermitian and skew-symmetric respectively, as eq. (4) requires.
+ * dtype: storage precision of the caller's a11/a12 or U/W arrays (JTRLAN_C128 = double2,
+ *   JTRLAN_C64 = float2).  jtrlan_create converts them to the precision the solve needs.
+ * Ownership: jtrlan_create copies the operator into buffers the context owns; the caller may
+ *   free or reuse its arrays as soon as jtrlan_create returns. */
+typedef struct {
+  int kind;
+  int dtype;
+  int64_t n;          /* vector length; even.  Stencil: must equal 6 * volume. */
+  int dims[4];        /* stencil only */
+  double m0;          /* stencil only: diagonal mass term of A11 */
+  double kappa;       /* stencil only: strength of the A12 hopping term */
+  const void* a11;    /* dense only */
+  const void* a12;    /* dense only */
+  const void* U;      /* stencil only */
+  const void* W;      /* stencil only */
+} jtrlan_operator;
+
+/* Parameters of Algorithm 1.
+ *   nev: wanted eigenvalues (one per J pair), 0 < nev < m.
+ *   m: maximum Krylov dimension, m < n/2.  mwin: restart window, k = min(icnv + mwin, m - 1)
+ *   (eq. (29)), 0 <= mwin.
+ *   tol: convergence threshold on ||A x - lambda x|| with ||x|| = 1 (Algorithm 1, normal mode).
+ *   which: JTRLAN_SMALLEST (smallest algebraic) or JTRLAN_LARGEST.
+ *   precision: JTRLAN_FP64 (plain FP64 arithmetic throughout).  JTRLAN_MIXED is reserved.
+ *   max_restarts: bound on outer iterations (N_conv); 0 selects 1000.
+ *   gs_max_passes: bound on Gram-Schmidt passes per Lanczos step (Algorithm 2 has none);
+ *     0 selects 3.
+ *   v1: optional start vector (n complex in the operator's dtype, host or device); NULL gives
+ *     v1 = (1, ..., 1)/sqrt(n) as in Algorithm 1.  It is normalised by the library.
+ *   check_jsym: if nonzero, jtrlan_create tests Lemma 1, |(J v*)^H A v| <= 1e-10 ||A v|| ||v||,
+ *     on a fixed pseudo-random v and fails with JTRLAN_ENOTJSYM otherwise.
+ *   profile: if nonzero, jtrlan_solve brackets every kernel launch with CUDA events on the context
+ *     stream and sums the device time per kernel class (read with jtrlan_get_profile).  This adds
+ *     two event records per launch; leave it off for timed runs. */
+typedef struct {
+  int nev;
+  int m;
+  int mwin;
+  double tol;
+  int which;
+  int precision;
+  int max_restarts;
+  int gs_max_passes;
+  const void* v1;
+  int check_jsym;
+  int profile;        /* nonzero: time every kernel launch with CUDA events (jtrlan_get_profile) */
+} jtrlan_params;
+
+/* Counters of the last solve (Sec. 3 counts only the Lanczos-step products as N_MV). */
+typedef struct {
+  int64_t n_matvec;        /* N_MV: products A v_j inside Algorithm 2 */
+  int64_t n_resid_matvec;  /* products for the true residuals of Algorithm 1 (not in N_MV) */
+  int64_t n_gs_passes;     /* Gram-Schmidt passes over [V, W] */
+  int n_restarts;          /* N_conv: outer iterations */
+  int icnv;                /* converged pairs at exit */
+  double solve_ms;         /* wall time of jtrlan_solve on the host clock */
+  int64_t n_launches;      /* CUDA kernels launched by the solve */
+} jtrlan_stats;
+
+/* Per-kernel-class profile of the last solve (filled when jtrlan_params.profile was set; the
+ * launch counts are always filled).  work[] holds the algorithmic work of each class:
+ *   "matvec": products A v (Lanczos steps) times the units of one product -- lattice sites for a
+ *     stencil, (n/2)^2 block entries for a dense operator;
+ *   "gs_first", "gs_dot", "gs_update": row-pair x basis-column products (each reads one complex
+ *     number of each half of a basis vector and does four complex multiply-adds);
+ *   "rotate": (2n) x m x kk real multiply-adds of V_m Z;  "resid": products A v as for "matvec";
+ *   other classes: 0. */
+#define JTRLAN_MAX_KERNEL_CLASSES 16
+typedef struct {
+  int n_classes;
+  const char* names[JTRLAN_MAX_KERNEL_CLASSES];
+  double ms[JTRLAN_MAX_KERNEL_CLASSES];
+  int64_t launches[JTRLAN_MAX_KERNEL_CLASSES];
+  double work[JTRLAN_MAX_KERNEL_CLASSES];
+} jtrlan_profile;
+
+typedef struct jtrlan_ctx jtrlan_ctx;  /* opaque; owned by the library */
+
+/* Validates op and params, allocates the context's device buffers and copies the operator.
+ * cuda_stream: a cudaStream_t (or NULL) on which every later call enqueues its work.
+ * Errors: JTRLAN_EINVAL (odd n, n != 6V for a stencil, nev/m/mwin out of range, null
+ * pointers), JTRLAN_ENOMEM, JTRLAN_ECUDA, JTRLAN_ENOTJSYM.  *out is NULL on failure. */
+jtrlan_status jtrlan_create(const jtrlan_operator* op, const jtrlan_params* params,
+                            void* cuda_stream, jtrlan_ctx** out);
+
+/* y = A x in the canonical layout, both device pointers of n complex numbers in the context's
+ * working precision (double2 for JTRLAN_FP64).  Enqueued on the context stream; no sync.
+ * This is the Algorithm 2 product A v_j.  Errors: JTRLAN_EINVAL (null), JTRLAN_ECUDA. */
+jtrlan_status jtrlan_apply(jtrlan_ctx* ctx, const void* x, void* y);
+
+/* Runs Algorithm 1 (TRLAN-JSYM) with the Lanczos step of Algorithm 2 until nev pairs have a
+ * true residual below tol.  Synchronises the context stream once per restart.  stats may be
+ * NULL.  Errors: JTRLAN_ENOCONV, JTRLAN_EBREAKDOWN, JTRLAN_ECUDA. */
+jtrlan_status jtrlan_solve(jtrlan_ctx* ctx, jtrlan_stats* stats);
+
+/* Copies the converged pairs of the last successful solve, sorted by eigenvalue (ascending for
+ * JTRLAN_SMALLEST, descending for JTRLAN_LARGEST).
+ *   evals: host array of nev doubles (may be NULL).
+ *   evecs: host or device array, column-major n x nev (or n x 2nev if with_partners), in the
+ *     context's working precision (double2 for JTRLAN_FP64); may be NULL.  With partners,
+ *     column nev + i holds y_i = J x_i^* (eq. (2)).
+ *   res: host array of nev doubles, the true residuals ||A x_i - lambda_i x_i|| (may be NULL).
+ * Synchronises the context stream.  Errors: JTRLAN_ESTATE if no solve has succeeded. */
+jtrlan_status jtrlan_pairs(jtrlan_ctx* ctx, int with_partners, double* evals, void* evecs,
+                           double* res);
+
+/* Copies the per-kernel profile of the last solve into *out.  Errors: JTRLAN_EINVAL (null). */
+jtrlan_status jtrlan_get_profile(jtrlan_ctx* ctx, jtrlan_profile* out);
+
+/* Frees everything the context owns (after synchronising its stream).  NULL is a no-op. */
+void jtrlan_destroy(jtrlan_ctx* ctx);
+
+/* Static text for a status code. */
+const char* jtrlan_status_string(jtrlan_status s);
+
+/* Thread-local text describing the last failure on this host thread ("" if none). */
+const char* jtrlan_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JTRLAN_H */

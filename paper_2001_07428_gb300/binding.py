@@ -1,0 +1,171 @@
+"""Thin ctypes binding over libjtrlan.so (C ABI in include/jtrlan.h).
+
+Only argument marshalling lives here: every step of the solver runs in the library's CUDA
+kernels.  Buffers are passed as raw pointers -- ``torch.Tensor.data_ptr()`` for device (or pinned
+host) tensors, ``numpy.ndarray.ctypes.data`` for host arrays.  There is no CPU fallback: if the
+library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libjtrlan.so")
+
+JTRLAN_OK, JTRLAN_EINVAL, JTRLAN_ENOMEM, JTRLAN_ECUDA, JTRLAN_ENOTJSYM = 0, 1, 2, 3, 4
+JTRLAN_EBREAKDOWN, JTRLAN_ENOCONV, JTRLAN_ETIMEOUT, JTRLAN_ESTATE = 5, 6, 7, 8
+JTRLAN_DENSE, JTRLAN_STENCIL4D = 0, 1
+JTRLAN_C128, JTRLAN_C64 = 0, 1
+JTRLAN_SMALLEST, JTRLAN_LARGEST = 0, 1
+JTRLAN_FP64, JTRLAN_MIXED = 0, 1
+
+EXPORTED = ["jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
+            "jtrlan_destroy", "jtrlan_status_string", "jtrlan_last_error"]
+
+
+class jtrlan_operator(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("n", ctypes.c_int64),
+                ("dims", ctypes.c_int * 4), ("m0", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("a11", ctypes.c_void_p), ("a12", ctypes.c_void_p), ("U", ctypes.c_void_p),
+                ("W", ctypes.c_void_p)]
+
+
+class jtrlan_params(ctypes.Structure):
+    _fields_ = [("nev", ctypes.c_int), ("m", ctypes.c_int), ("mwin", ctypes.c_int),
+                ("tol", ctypes.c_double), ("which", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_restarts", ctypes.c_int), ("gs_max_passes", ctypes.c_int),
+                ("v1", ctypes.c_void_p), ("check_jsym", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class jtrlan_stats(ctypes.Structure):
+    _fields_ = [("n_matvec", ctypes.c_int64), ("n_resid_matvec", ctypes.c_int64),
+                ("n_gs_passes", ctypes.c_int64), ("n_restarts", ctypes.c_int),
+                ("icnv", ctypes.c_int), ("solve_ms", ctypes.c_double), ("n_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+MAX_KERNEL_CLASSES = 16
+
+
+class jtrlan_profile(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int), ("names", ctypes.c_char_p * MAX_KERNEL_CLASSES),
+                ("ms", ctypes.c_double * MAX_KERNEL_CLASSES),
+                ("launches", ctypes.c_int64 * MAX_KERNEL_CLASSES),
+                ("work", ctypes.c_double * MAX_KERNEL_CLASSES)]
+
+    def as_dict(self):
+        return {self.names[i].decode(): dict(ms=self.ms[i], launches=self.launches[i], work=self.work[i])
+                for i in range(self.n_classes)}
+
+
+class JTRLanError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libjtrlan.so (once); raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(python -m paper_2001_07428_gb300.build)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    lib.jtrlan_create.argtypes = [P(jtrlan_operator), P(jtrlan_params), ctypes.c_void_p,
+                                  P(ctypes.c_void_p)]
+    lib.jtrlan_apply.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.jtrlan_solve.argtypes = [ctypes.c_void_p, P(jtrlan_stats)]
+    lib.jtrlan_pairs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p]
+    lib.jtrlan_get_profile.argtypes = [ctypes.c_void_p, P(jtrlan_profile)]
+    lib.jtrlan_destroy.argtypes = [ctypes.c_void_p]
+    lib.jtrlan_destroy.restype = None
+    lib.jtrlan_status_string.argtypes = [ctypes.c_int]
+    lib.jtrlan_status_string.restype = ctypes.c_char_p
+    lib.jtrlan_last_error.argtypes = []
+    lib.jtrlan_last_error.restype = ctypes.c_char_p
+    for f in ("jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != JTRLAN_OK:
+        lib = load()
+        msg = lib.jtrlan_last_error().decode() or lib.jtrlan_status_string(status).decode()
+        raise JTRLanError(status, msg)
+
+
+# ---------------------------------------------------------------- the C calls, same names
+def jtrlan_create(op: jtrlan_operator, params: jtrlan_params, stream: int = 0) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(load().jtrlan_create(ctypes.byref(op), ctypes.byref(params), ctypes.c_void_p(stream),
+                                ctypes.byref(ctx)))
+    return ctx
+
+
+def jtrlan_apply(ctx, x_ptr: int, y_ptr: int):
+    _check(load().jtrlan_apply(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr)))
+
+
+def jtrlan_solve(ctx) -> dict:
+    st = jtrlan_stats()
+    _check(load().jtrlan_solve(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def jtrlan_pairs(ctx, with_partners: int, evals_ptr, evecs_ptr, res_ptr):
+    _check(load().jtrlan_pairs(ctx, int(with_partners), evals_ptr, evecs_ptr, res_ptr))
+
+
+def jtrlan_get_profile(ctx) -> dict:
+    pr = jtrlan_profile()
+    _check(load().jtrlan_get_profile(ctx, ctypes.byref(pr)))
+    return pr.as_dict()
+
+
+def jtrlan_destroy(ctx):
+    if ctx:
+        load().jtrlan_destroy(ctx)
+
+
+# ---------------------------------------------------------------- builders for the structs
+def stencil_operator(dims, m0, kappa, U_ptr, W_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
+    op = jtrlan_operator()
+    op.kind, op.dtype = JTRLAN_STENCIL4D, dtype
+    vol = int(dims[0]) * int(dims[1]) * int(dims[2]) * int(dims[3])
+    op.n = 6 * vol
+    for d in range(4):
+        op.dims[d] = int(dims[d])
+    op.m0, op.kappa = float(m0), float(kappa)
+    op.U, op.W = U_ptr, W_ptr
+    return op
+
+
+def dense_operator(n, a11_ptr, a12_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
+    op = jtrlan_operator()
+    op.kind, op.dtype, op.n = JTRLAN_DENSE, dtype, int(n)
+    op.a11, op.a12 = a11_ptr, a12_ptr
+    return op
+
+
+def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_restarts=0,
+           gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0) -> jtrlan_params:
+    p = jtrlan_params()
+    p.nev, p.m, p.mwin, p.tol = int(nev), int(m), int(mwin), float(tol)
+    p.which, p.precision = int(which), int(precision)
+    p.max_restarts, p.gs_max_passes = int(max_restarts), int(gs_max_passes)
+    p.v1 = v1_ptr
+    p.check_jsym = int(check_jsym)
+    p.profile = int(profile)
+    return p

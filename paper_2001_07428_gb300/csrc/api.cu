@@ -1,0 +1,557 @@
+// api.cu -- the C ABI of libjtrlan (include/jtrlan.h): context management and the host side of
+// Algorithm 1 (TRLAN-JSYM).  Every vector operation runs in the kernels of matvec.cu, gs.cu and
+// ritz.cu; the host keeps only the O(m) bookkeeping of the restart (which Ritz pairs to test,
+// the converged-first ordering, k of eq. (29)) and reads back O(m) numbers once per restart.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "../../include/jtrlan.h"
+
+using namespace jtr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+jtrlan_status fail(jtrlan_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define JT_CUDA(expr)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(e_ == cudaErrorMemoryAllocation ? JTRLAN_ENOMEM : JTRLAN_ECUDA,                  \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                             \
+  } while (0)
+
+__global__ void c64_to_c128_kernel(const float2* in, double2* out, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+const char* kTagNames[K_NTAGS] = {"matvec", "gs_first", "gs_reduce", "gs_update", "gs_dot", "gs_normalize",
+                                  "ritz", "rotate", "resid", "shrink", "other"};
+
+// Optional per-launch CUDA-event timing, harvested at the host synchronisation points.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> tag;
+  size_t used = 0;
+  double ms[K_NTAGS] = {};
+  cudaError_t begin(int t, cudaStream_t s) {
+    if (!on) return cudaSuccess;
+    if (2 * used + 2 > ev.size()) {
+      const size_t add = 512;
+      for (size_t i = 0; i < 2 * add; ++i) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ev.push_back(e);
+      }
+      tag.resize(ev.size() / 2);
+    }
+    tag[used] = t;
+    return cudaEventRecord(ev[2 * used], s);
+  }
+  cudaError_t end(cudaStream_t s) {
+    if (!on) return cudaSuccess;
+    cudaError_t r = cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+    return r;
+  }
+  cudaError_t harvest() {  // call after the stream has been synchronised
+    for (size_t i = 0; i < used; ++i) {
+      float f = 0.f;
+      cudaError_t r = cudaEventElapsedTime(&f, ev[2 * i], ev[2 * i + 1]);
+      if (r != cudaSuccess) return r;
+      ms[tag[i]] += f;
+    }
+    used = 0;
+    return cudaSuccess;
+  }
+  ~Profiler() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace
+
+struct jtrlan_ctx {
+  jtrlan_operator opd{};
+  jtrlan_params prm{};
+  cudaStream_t stream = nullptr;
+  OpDev op{};
+  int64_t n = 0, h = 0;
+  int m = 0, nev = 0, mwin = 0, kk = 0, max_restarts = 0, gs_passes = 0;
+  size_t csize = sizeof(double2);  // bytes per complex number of the working precision
+  std::vector<void*> owned;        // device allocations
+  std::vector<void*> owned_host;   // pinned host allocations
+  void* V = nullptr;
+  void* Vtmp = nullptr;
+  void* y = nullptr;
+  double* T = nullptr;
+  double* lam = nullptr;
+  double* Z = nullptr;
+  double* ritz_ws = nullptr;
+  double* work_ritz() { return ritz_ws; }
+  double* part_dot = nullptr;
+  double* part_nrm = nullptr;
+  coef4* coef = nullptr;
+  StepState* st = nullptr;
+  double* alpha_part = nullptr;
+  double* resid_part = nullptr;
+  double* d_res = nullptr;
+  double* d_candlam = nullptr;
+  int* d_cand = nullptr;
+  int* d_perm = nullptr;
+  int* d_order = nullptr;
+  double* d_rep = nullptr;
+  double* d_misc = nullptr;
+  // pinned staging
+  double* h_rep = nullptr;
+  double* h_T = nullptr;
+  double* h_res = nullptr;
+  double* h_candlam = nullptr;
+  int* h_cand = nullptr;
+  int* h_perm = nullptr;
+  int* h_order = nullptr;
+  double* h_misc = nullptr;
+  int mv_nblk = 0, gs_nblk = 0, gs_rpb = 0;
+  Profiler prof;
+  int64_t nl[K_NTAGS] = {};        // launches per kernel class in the last solve
+  double work[K_NTAGS] = {};       // algorithmic work per kernel class in the last solve
+  // results of the last solve
+  bool solved = false;
+  std::vector<double> ev, res;
+  jtrlan_stats stats{};
+
+  template <typename T_>
+  jtrlan_status dalloc(T_** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) return fail(JTRLAN_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    owned.push_back(q);
+    *p = (T_*)q;
+    return JTRLAN_OK;
+  }
+  template <typename T_>
+  jtrlan_status halloc(T_** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocHost(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) return fail(JTRLAN_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    owned_host.push_back(q);
+    *p = (T_*)q;
+    return JTRLAN_OK;
+  }
+  ~jtrlan_ctx() {
+    cudaStreamSynchronize(stream);
+    for (void* p : owned) cudaFree(p);
+    for (void* p : owned_host) cudaFreeHost(p);
+  }
+};
+
+namespace {
+
+#define JT_TRY(expr)                       \
+  do {                                     \
+    jtrlan_status s_ = (expr);             \
+    if (s_ != JTRLAN_OK) return s_;        \
+  } while (0)
+
+// Copies `count` complex numbers of the caller's dtype (host or device) into an owned FP64 buffer.
+jtrlan_status upload_c128(jtrlan_ctx* c, const void* src, int dtype, int64_t count, void** dst) {
+  double2* d = nullptr;
+  JT_TRY(c->dalloc(&d, (size_t)count * sizeof(double2)));
+  if (dtype == JTRLAN_C128) {
+    JT_CUDA(cudaMemcpyAsync(d, src, (size_t)count * sizeof(double2), cudaMemcpyDefault, c->stream));
+  } else {
+    float2* tmp = nullptr;
+    JT_CUDA(cudaMallocAsync((void**)&tmp, (size_t)count * sizeof(float2), c->stream));
+    JT_CUDA(cudaMemcpyAsync(tmp, src, (size_t)count * sizeof(float2), cudaMemcpyDefault, c->stream));
+    c64_to_c128_kernel<<<1024, 256, 0, c->stream>>>(tmp, d, count);
+    JT_CUDA(cudaGetLastError());
+    JT_CUDA(cudaFreeAsync(tmp, c->stream));
+  }
+  *dst = d;
+  return JTRLAN_OK;
+}
+
+jtrlan_status validate(const jtrlan_operator* op, const jtrlan_params* p) {
+  if (!op || !p) return fail(JTRLAN_EINVAL, "null operator or params");
+  if (op->n <= 0 || (op->n & 1)) return fail(JTRLAN_EINVAL, "n must be positive and even");
+  if (op->dtype != JTRLAN_C128 && op->dtype != JTRLAN_C64) return fail(JTRLAN_EINVAL, "unknown dtype");
+  if (op->kind == JTRLAN_STENCIL4D) {
+    int64_t vol = 1;
+    for (int d = 0; d < 4; ++d) {
+      if (op->dims[d] < 1) return fail(JTRLAN_EINVAL, "lattice extents must be >= 1");
+      vol *= op->dims[d];
+    }
+    if (op->n != 6 * vol) return fail(JTRLAN_EINVAL, "stencil n must equal 6 * volume");
+    if (!op->U || !op->W) return fail(JTRLAN_EINVAL, "null link field");
+  } else if (op->kind == JTRLAN_DENSE) {
+    if (!op->a11 || !op->a12) return fail(JTRLAN_EINVAL, "null dense block");
+  } else {
+    return fail(JTRLAN_EINVAL, "unknown operator kind");
+  }
+  if (p->nev <= 0 || p->m <= p->nev) return fail(JTRLAN_EINVAL, "need 0 < nev < m");
+  if ((int64_t)p->m >= op->n / 2) return fail(JTRLAN_EINVAL, "need m < n/2");
+  if (p->m > 1023) return fail(JTRLAN_EINVAL, "m > 1023 is not supported by the Ritz kernel");
+  if (p->mwin < 0) return fail(JTRLAN_EINVAL, "need mwin >= 0");
+  if (!(p->tol > 0.0)) return fail(JTRLAN_EINVAL, "need tol > 0");
+  if (p->which != JTRLAN_SMALLEST && p->which != JTRLAN_LARGEST) return fail(JTRLAN_EINVAL, "unknown which");
+  if (p->precision != JTRLAN_FP64) return fail(JTRLAN_EINVAL, "only JTRLAN_FP64 is implemented");
+  if (p->gs_max_passes < 0 || p->gs_max_passes > 7) return fail(JTRLAN_EINVAL, "gs_max_passes must be 0..7");
+  if (p->max_restarts < 0) return fail(JTRLAN_EINVAL, "max_restarts must be >= 0");
+  return JTRLAN_OK;
+}
+
+jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, void* stream, jtrlan_ctx** out) {
+  JT_TRY(validate(op, prm));
+  jtrlan_ctx* c = new (std::nothrow) jtrlan_ctx();
+  if (!c) return fail(JTRLAN_ENOMEM, "host allocation failed");
+  *out = c;  // released by the caller on failure
+  c->opd = *op;
+  c->prm = *prm;
+  c->stream = (cudaStream_t)stream;
+  c->n = op->n;
+  c->h = op->n / 2;
+  c->m = prm->m;
+  c->nev = prm->nev;
+  c->mwin = prm->mwin;
+  c->kk = std::min(prm->nev + prm->mwin, prm->m - 1);
+  c->max_restarts = prm->max_restarts ? prm->max_restarts : 1000;
+  c->gs_passes = prm->gs_max_passes ? prm->gs_max_passes : 3;
+  OpDev& o = c->op;
+  o.kind = op->kind;
+  o.n = c->n;
+  o.h = c->h;
+  o.m0 = op->m0;
+  o.kappa = op->kappa;
+  o.vol = 1;
+  for (int d = 0; d < 4; ++d) { o.dims[d] = op->dims[d]; if (op->kind == JTRLAN_STENCIL4D) o.vol *= op->dims[d]; }
+  if (op->kind == JTRLAN_STENCIL4D) {
+    void *u = nullptr, *w = nullptr;
+    JT_TRY(upload_c128(c, op->U, op->dtype, 4 * o.vol * 9, &u));
+    JT_TRY(upload_c128(c, op->W, op->dtype, 4 * o.vol * 9, &w));
+    o.U = u; o.W = w;
+  } else {
+    void *a = nullptr, *b = nullptr;
+    JT_TRY(upload_c128(c, op->a11, op->dtype, c->h * c->h, &a));
+    JT_TRY(upload_c128(c, op->a12, op->dtype, c->h * c->h, &b));
+    o.a11 = a; o.a12 = b;
+  }
+  const int m = c->m;
+  const int mp = m + (m & 1);
+  c->mv_nblk = matvec_blocks(o);
+  c->gs_nblk = gs_blocks(c->h, &c->gs_rpb);
+  const size_t cs = c->csize;
+  JT_TRY(c->dalloc(&c->V, (size_t)c->n * (m + 1) * cs));
+  JT_TRY(c->dalloc(&c->Vtmp, (size_t)c->n * std::max(c->kk, 1) * cs));
+  JT_TRY(c->dalloc(&c->y, (size_t)c->n * cs));
+  JT_TRY(c->dalloc(&c->T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
+  JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));
+  JT_TRY(c->dalloc(&c->Z, (size_t)m * m * sizeof(double)));
+  JT_TRY(c->dalloc(&c->ritz_ws, (size_t)2 * mp * mp * sizeof(double)));
+  JT_TRY(c->dalloc(&c->part_dot, (size_t)(m + 1) * c->gs_nblk * sizeof(coef4)));
+  JT_TRY(c->dalloc(&c->part_nrm, (size_t)c->gs_nblk * sizeof(double)));
+  JT_TRY(c->dalloc(&c->coef, (size_t)(m + 1) * sizeof(coef4)));
+  JT_TRY(c->dalloc(&c->st, sizeof(StepState)));
+  JT_TRY(c->dalloc(&c->alpha_part, (size_t)c->mv_nblk * sizeof(double2)));
+  JT_TRY(c->dalloc(&c->resid_part, (size_t)c->mv_nblk * c->nev * sizeof(double)));
+  JT_TRY(c->dalloc(&c->d_res, (size_t)c->nev * sizeof(double)));
+  JT_TRY(c->dalloc(&c->d_candlam, (size_t)c->nev * sizeof(double)));
+  JT_TRY(c->dalloc(&c->d_cand, (size_t)c->nev * sizeof(int)));
+  JT_TRY(c->dalloc(&c->d_perm, (size_t)m * sizeof(int)));
+  JT_TRY(c->dalloc(&c->d_order, (size_t)c->nev * sizeof(int)));
+  JT_TRY(c->dalloc(&c->d_rep, (size_t)(2 * m + 8) * sizeof(double)));
+  JT_TRY(c->dalloc(&c->d_misc, 16 * sizeof(double)));
+  JT_TRY(c->halloc(&c->h_rep, (size_t)(2 * m + 8) * sizeof(double)));
+  JT_TRY(c->halloc(&c->h_T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
+  JT_TRY(c->halloc(&c->h_res, (size_t)c->nev * sizeof(double)));
+  JT_TRY(c->halloc(&c->h_candlam, (size_t)c->nev * sizeof(double)));
+  JT_TRY(c->halloc(&c->h_cand, (size_t)c->nev * sizeof(int)));
+  JT_TRY(c->halloc(&c->h_perm, (size_t)m * sizeof(int)));
+  JT_TRY(c->halloc(&c->h_order, (size_t)c->nev * sizeof(int)));
+  JT_TRY(c->halloc(&c->h_misc, 16 * sizeof(double)));
+  if (prm->check_jsym) {  // Lemma 1: (J v^*)^H A v = 0 for any v
+    JT_CUDA(launch_fill_random<double>(c->Vtmp, c->n, 0x5eed1234ull, c->stream));
+    JT_CUDA(launch_matvec<double>(o, (const double2*)c->Vtmp, (double2*)c->y, MV_PLAIN, nullptr, nullptr, nullptr, 0,
+                                  0, nullptr, c->stream));
+    JT_CUDA(launch_jsym_check<double>(c->Vtmp, c->y, c->h, c->d_misc, c->stream));
+    JT_CUDA(cudaMemcpyAsync(c->h_misc, c->d_misc, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    JT_CUDA(cudaStreamSynchronize(c->stream));
+    const double wAv = std::hypot(c->h_misc[0], c->h_misc[1]);
+    const double scale = std::sqrt(c->h_misc[2] * c->h_misc[3]);
+    if (!(wAv <= 1e-10 * scale)) {
+      char buf[160];
+      std::snprintf(buf, sizeof buf, "Lemma 1 check failed: |(Jv*)^H A v| = %.3e vs ||Av|| ||v|| = %.3e", wAv, scale);
+      return fail(JTRLAN_ENOTJSYM, buf);
+    }
+  }
+  JT_CUDA(cudaStreamSynchronize(c->stream));
+  return JTRLAN_OK;
+}
+
+inline void* col(void* base, int64_t n, int j, size_t cs) { return (char*)base + (size_t)j * n * cs; }
+
+jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
+  const auto t0 = std::chrono::steady_clock::now();
+  c->solved = false;
+  const int m = c->m, nev = c->nev, ldt = m + 1;
+  const int64_t n = c->n;
+  const size_t cs = c->csize;
+  cudaStream_t s = c->stream;
+  jtrlan_stats stt{};
+  c->prof.on = c->prm.profile != 0;
+  c->prof.used = 0;
+  for (int t = 0; t < K_NTAGS; ++t) { c->prof.ms[t] = 0; c->nl[t] = 0; c->work[t] = 0; }
+#define LAUNCH(tag, expr)                  \
+  do {                                     \
+    JT_CUDA(c->prof.begin((tag), s));      \
+    JT_CUDA(expr);                         \
+    JT_CUDA(c->prof.end(s));               \
+    c->nl[(tag)] += 1;                     \
+  } while (0)
+  JT_CUDA(cudaMemsetAsync(c->st, 0, sizeof(StepState), s));
+  JT_CUDA(cudaMemsetAsync(c->T, 0, (size_t)ldt * ldt * sizeof(double), s));
+  if (c->prm.v1) {
+    if (c->opd.dtype != JTRLAN_C128) return fail(JTRLAN_EINVAL, "v1 must be complex128 for the FP64 solver");
+    JT_CUDA(cudaMemcpyAsync(c->V, c->prm.v1, (size_t)n * cs, cudaMemcpyDefault, s));
+    LAUNCH(K_OTHER, launch_normalize_col<double>(c->V, n, c->part_nrm, c->gs_nblk, s));
+    c->nl[K_OTHER] += 1;  // two kernels
+  } else {
+    LAUNCH(K_OTHER, launch_fill_ones<double>(c->V, n, s));  // v_1 = 1 / ||1||
+  }
+  GSArgs a{};
+  a.V = c->V; a.n = n; a.h = c->h; a.y = c->y; a.part_dot = c->part_dot; a.part_nrm = c->part_nrm;
+  a.coef = c->coef; a.st = c->st; a.T = c->T; a.ldt = ldt; a.m = m; a.nblk = c->gs_nblk;
+  a.rows_per_block = c->gs_rpb;
+  const double mv_units = c->op.kind == JTRLAN_STENCIL4D ? (double)c->op.vol : (double)c->h * (double)c->h;
+  std::vector<double> ev(nev), res(nev, INFINITY), res_est(nev), lamv(m), arrow(m);
+  std::vector<char> conv(nev);
+  std::vector<int> perm(m);
+  int k = 0, icnv = 0;
+  for (int restart = 0; restart < c->max_restarts; ++restart) {
+    // ---- Algorithm 2: m - k Lanczos steps, no host synchronisation inside
+    for (int j = k; j < m; ++j) {
+      LAUNCH(K_MATVEC, launch_matvec<double>(c->op, (const double2*)col(c->V, n, j, cs), (double2*)c->y, MV_ALPHA,
+                                             c->alpha_part, nullptr, nullptr, 0, 0, nullptr, s));
+      a.j = j;
+      LAUNCH(K_GS_FIRST, launch_gs_first<double>(a, (const double2*)c->alpha_part, c->mv_nblk, s));
+      LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
+      LAUNCH(K_GS_UPDATE, launch_gs_update<double>(a, s));
+      for (int pass = 2; pass <= c->gs_passes; ++pass) {
+        LAUNCH(K_GS_DOT, launch_gs_dot<double>(a, pass, s));
+        LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
+        LAUNCH(K_GS_UPDATE, launch_gs_update<double>(a, s));
+      }
+      LAUNCH(K_GS_NORMALIZE, launch_gs_normalize<double>(a, s));
+    }
+    stt.n_matvec += m - k;
+    c->work[K_MATVEC] += (double)(m - k) * mv_units;
+    stt.n_restarts += 1;
+    // ---- Rayleigh-Ritz: T_m = Z Lambda Z^T, sorted; V_m Z into Vtmp
+    LAUNCH(K_RITZ, launch_ritz(c->T, ldt, m, c->prm.which, c->lam, c->Z, c->work_ritz(), s));
+    LAUNCH(K_ROTATE, launch_rotate<double>(c->V, n, m, c->Z, c->kk, c->Vtmp, s));
+    c->work[K_ROTATE] += 2.0 * (double)n * m * c->kk;
+    LAUNCH(K_OTHER, launch_report(c->lam, c->Z, m, c->T, ldt, c->st, c->d_rep, s));
+    JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * m + 7) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    JT_CUDA(cudaStreamSynchronize(s));
+    JT_CUDA(c->prof.harvest());
+    stt.n_gs_passes = (int64_t)c->h_rep[2 * m + 2];
+    c->work[K_GS_FIRST] = c->h_rep[2 * m + 4];
+    c->work[K_GS_DOT] = c->h_rep[2 * m + 5];
+    c->work[K_GS_UPDATE] = c->h_rep[2 * m + 6];
+    if (c->h_rep[2 * m + 1] != 0.0) {
+      c->stats = stt;
+      if (stats_out) *stats_out = stt;
+      return fail(JTRLAN_EBREAKDOWN, "Lanczos breakdown: beta below 1e-14 max|T|");
+    }
+    const double beta_m = c->h_rep[2 * m];
+    for (int i = 0; i < m; ++i) {
+      lamv[i] = c->h_rep[i];
+      arrow[i] = beta_m * c->h_rep[m + i];   // t_{m+1,i} = t_{m+1,m} z_{m,i}
+    }
+    int ncand = 0;
+    for (int i = 0; i < nev; ++i) {
+      ev[i] = lamv[i];
+      res_est[i] = std::fabs(arrow[i]);
+      conv[i] = 0;                            // is_convd reset every outer iteration
+      if (res_est[i] < c->prm.tol) { c->h_cand[ncand] = i; c->h_candlam[ncand] = ev[i]; ++ncand; }
+    }
+    if (ncand > 0) {  // true residuals ||A v_i - ev_i v_i|| of the candidates
+      JT_CUDA(cudaMemcpyAsync(c->d_cand, c->h_cand, ncand * sizeof(int), cudaMemcpyHostToDevice, s));
+      JT_CUDA(cudaMemcpyAsync(c->d_candlam, c->h_candlam, ncand * sizeof(double), cudaMemcpyHostToDevice, s));
+      LAUNCH(K_RESID, launch_matvec<double>(c->op, (const double2*)c->Vtmp, nullptr, MV_RESID, c->resid_part, c->d_cand,
+                                            c->d_candlam, ncand, n, nullptr, s));
+      c->work[K_RESID] += (double)ncand * mv_units;
+      LAUNCH(K_OTHER, launch_reduce_norms(c->resid_part, c->mv_nblk, ncand, c->d_res, s));
+      JT_CUDA(cudaMemcpyAsync(c->h_res, c->d_res, ncand * sizeof(double), cudaMemcpyDeviceToHost, s));
+      JT_CUDA(cudaStreamSynchronize(s));
+      JT_CUDA(c->prof.harvest());
+      stt.n_resid_matvec += ncand;
+      for (int q = 0; q < ncand; ++q) {
+        const int i = c->h_cand[q];
+        res[i] = c->h_res[q];
+        conv[i] = res[i] < c->prm.tol;
+      }
+    }
+    // converged pairs to the top (stable), identity beyond nev
+    int w = 0;
+    for (int i = 0; i < nev; ++i) if (conv[i]) perm[w++] = i;
+    icnv = w;
+    for (int i = 0; i < nev; ++i) if (!conv[i]) perm[w++] = i;
+    for (int i = nev; i < m; ++i) perm[i] = i;
+    std::vector<double> ev2(nev), res2(nev), lam2(m), arrow2(m);
+    for (int i = 0; i < m; ++i) { lam2[i] = lamv[perm[i]]; arrow2[i] = arrow[perm[i]]; }
+    for (int i = 0; i < nev; ++i) { ev2[i] = ev[perm[i]]; res2[i] = res[perm[i]]; }
+    ev = ev2; res = res2; lamv = lam2; arrow = arrow2;
+    for (int i = 0; i < icnv; ++i) arrow[i] = 0.0;   // decouple the converged subspace
+    if (icnv == nev) {
+      for (int i = 0; i < m; ++i) c->h_perm[i] = perm[i];
+      JT_CUDA(cudaMemcpyAsync(c->d_perm, c->h_perm, m * sizeof(int), cudaMemcpyHostToDevice, s));
+      LAUNCH(K_SHRINK, launch_shrink<double>(c->V, c->Vtmp, n, c->d_perm, nev, m, s));
+      JT_CUDA(cudaStreamSynchronize(s));
+      JT_CUDA(c->prof.harvest());
+      break;
+    }
+    // ---- shrink to k + 1 (eq. (29)); T-bar = diag(lambda_1..k) with the arrow in row k+1
+    k = std::min(icnv + c->mwin, m - 1);
+    std::memset(c->h_T, 0, (size_t)ldt * ldt * sizeof(double));
+    double tmax = 0.0;
+    for (int i = 0; i < k; ++i) {
+      c->h_T[(size_t)i * ldt + i] = lamv[i];
+      c->h_T[(size_t)k * ldt + i] = arrow[i];
+      c->h_T[(size_t)i * ldt + k] = arrow[i];
+      tmax = std::max(tmax, std::max(std::fabs(lamv[i]), std::fabs(arrow[i])));
+    }
+    c->h_misc[0] = tmax;
+    for (int i = 0; i < m; ++i) c->h_perm[i] = perm[i];
+    JT_CUDA(cudaMemcpyAsync(c->T, c->h_T, (size_t)ldt * ldt * sizeof(double), cudaMemcpyHostToDevice, s));
+    JT_CUDA(cudaMemcpyAsync(&c->st->tmax, c->h_misc, sizeof(double), cudaMemcpyHostToDevice, s));
+    JT_CUDA(cudaMemcpyAsync(c->d_perm, c->h_perm, m * sizeof(int), cudaMemcpyHostToDevice, s));
+    LAUNCH(K_SHRINK, launch_shrink<double>(c->V, c->Vtmp, n, c->d_perm, k, m, s));  // and v_{k+1} = v_{m+1}
+  }
+#undef LAUNCH
+  stt.icnv = icnv;
+  for (int t = 0; t < K_NTAGS; ++t) stt.n_launches += c->nl[t];
+  stt.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  c->stats = stt;
+  if (stats_out) *stats_out = stt;
+  if (icnv != nev) return fail(JTRLAN_ENOCONV, "max_restarts reached before nev pairs converged");
+  c->ev = ev;
+  c->res = res;
+  c->solved = true;
+  return JTRLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jtrlan_status jtrlan_create(const jtrlan_operator* op, const jtrlan_params* params, void* cuda_stream,
+                            jtrlan_ctx** out) {
+  if (!out) return fail(JTRLAN_EINVAL, "null out pointer");
+  *out = nullptr;
+  jtrlan_ctx* c = nullptr;
+  jtrlan_status s = create_impl(op, params, cuda_stream, &c);
+  if (s != JTRLAN_OK) {
+    delete c;
+    return s;
+  }
+  *out = c;
+  g_last_error.clear();
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_apply(jtrlan_ctx* c, const void* x, void* y) {
+  if (!c || !x || !y) return fail(JTRLAN_EINVAL, "null argument");
+  JT_CUDA(launch_matvec<double>(c->op, (const double2*)x, (double2*)y, MV_PLAIN, nullptr, nullptr, nullptr, 0, 0,
+                                nullptr, c->stream));
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_solve(jtrlan_ctx* c, jtrlan_stats* stats) {
+  if (!c) return fail(JTRLAN_EINVAL, "null context");
+  return solve_impl(c, stats);
+}
+
+jtrlan_status jtrlan_pairs(jtrlan_ctx* c, int with_partners, double* evals, void* evecs, double* res) {
+  if (!c) return fail(JTRLAN_EINVAL, "null context");
+  if (!c->solved) return fail(JTRLAN_ESTATE, "no successful solve to report");
+  const int nev = c->nev;
+  std::vector<int> order(nev);
+  for (int i = 0; i < nev; ++i) order[i] = i;
+  const bool largest = c->prm.which == JTRLAN_LARGEST;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return largest ? c->ev[a] > c->ev[b] : c->ev[a] < c->ev[b];
+  });
+  for (int i = 0; i < nev; ++i) {
+    if (evals) evals[i] = c->ev[order[i]];
+    if (res) res[i] = c->res[order[i]];
+  }
+  if (evecs) {
+    for (int i = 0; i < nev; ++i) c->h_order[i] = order[i];
+    JT_CUDA(cudaMemcpyAsync(c->d_order, c->h_order, nev * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    const int ncols = with_partners ? 2 * nev : nev;
+    const size_t bytes = (size_t)c->n * ncols * c->csize;
+    cudaPointerAttributes attr{};
+    const bool dev = cudaPointerGetAttributes(&attr, evecs) == cudaSuccess &&
+                     (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (dev) {
+      JT_CUDA(launch_gather_pairs<double>(c->V, c->n, c->d_order, nev, with_partners, evecs, c->stream));
+    } else {
+      void* tmp = nullptr;
+      JT_CUDA(cudaMallocAsync(&tmp, bytes, c->stream));
+      JT_CUDA(launch_gather_pairs<double>(c->V, c->n, c->d_order, nev, with_partners, tmp, c->stream));
+      JT_CUDA(cudaMemcpyAsync(evecs, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
+      JT_CUDA(cudaFreeAsync(tmp, c->stream));
+    }
+  }
+  JT_CUDA(cudaStreamSynchronize(c->stream));
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_get_profile(jtrlan_ctx* c, jtrlan_profile* out) {
+  if (!c || !out) return fail(JTRLAN_EINVAL, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  out->n_classes = K_NTAGS;
+  for (int t = 0; t < K_NTAGS; ++t) {
+    out->names[t] = kTagNames[t];
+    out->ms[t] = c->prof.ms[t];
+    out->launches[t] = c->nl[t];
+    out->work[t] = c->work[t];
+  }
+  return JTRLAN_OK;
+}
+
+void jtrlan_destroy(jtrlan_ctx* c) { delete c; }
+
+const char* jtrlan_status_string(jtrlan_status s) {
+  switch (s) {
+    case JTRLAN_OK: return "ok";
+    case JTRLAN_EINVAL: return "invalid argument";
+    case JTRLAN_ENOMEM: return "out of memory";
+    case JTRLAN_ECUDA: return "CUDA error";
+    case JTRLAN_ENOTJSYM: return "operator is not Hermitian J-symmetric (Lemma 1 check)";
+    case JTRLAN_EBREAKDOWN: return "Lanczos breakdown";
+    case JTRLAN_ENOCONV: return "not converged within max_restarts";
+    case JTRLAN_ETIMEOUT: return "device wait timed out";
+    case JTRLAN_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* jtrlan_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

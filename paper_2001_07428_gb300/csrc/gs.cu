@@ -1,0 +1,379 @@
+// gs.cu -- the Gram-Schmidt part of the Lanczos step with J-symmetry (Algorithm 2).
+//
+// After y = A v_j (matvec.cu, which also leaves per-block partials of v_j^H y):
+//   t_{j,j} = Re(v_j^H y); y -= t_{j,j} v_j; b0 = ||y||
+//   repeat: orthogonalise y against W_j = J V_j^* and V_j; b1 = ||y||;
+//           stop when sqrt(2) b1 > b0, else b0 = b1           (gamma = sqrt(2))
+//   t_{j+1,j} = b1; v_{j+1} = y / b1                          (reading: divide by the final norm)
+//
+// W is never stored.  With v_i = [v1; v2] and w_i = J v_i^* = [-v2^*; v1^*]:
+//   c_v,i = v_i^H y = sum_p conj(v1) y1 + conj(v2) y2
+//   c_w,i = w_i^H y = sum_p (v1 y2 - v2 y1)          (no conjugate)
+//   y -= v_i c_v,i + w_i c_w,i:  y1 -= v1 c_v - conj(v2) c_w,  y2 -= v2 c_v + conj(v1) c_w
+// so one read of V gives both projections (classical Gram-Schmidt over [W_j, V_j], repeated by the
+// same sqrt(2) test as the paper's modified Gram-Schmidt loop).
+//
+// The data-dependent repeat runs without host synchronisation: every pass is launched, and each
+// kernel of a pass returns at once when the device-side flag st->done says the loop has exited.
+// All reductions use a fixed order, so results are reproducible run to run.
+#include "internal.h"
+
+namespace jtr {
+
+namespace {
+
+constexpr int kGsThreads = 256;   // 8 warps: lane = row pair in a tile of 32, warp = column group
+constexpr int kColGroups = kGsThreads / 32;
+constexpr int kRedThreads = 128;
+constexpr double kSqrt2 = 1.4142135623730951;
+
+template <typename R>
+__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1) {
+  using C = cplx<R>;
+  const C* V = (const C*)a.V;
+  const C* y = (const C*)a.y;
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int64_t n = a.n, h = a.h;
+  coef4* out = (coef4*)a.part_dot;
+  for (int i = q; i <= a.j; i += kColGroups) {
+    const C* vi = V + (int64_t)i * n;
+    C cv = mk<R>(0, 0), cw = mk<R>(0, 0);
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const C v1 = vi[p], v2 = vi[h + p], y1 = y[p], y2 = y[h + p];
+      cv = cfmac(v1, y1, cv);
+      cv = cfmac(v2, y2, cv);
+      cw = cfma(v1, y2, cw);
+      C nv2 = v2; nv2.x = -nv2.x; nv2.y = -nv2.y;
+      cw = cfma(nv2, y1, cw);
+    }
+    const double s0 = warp_sum((double)cv.x), s1 = warp_sum((double)cv.y);
+    const double s2 = warp_sum((double)cw.x), s3 = warp_sum((double)cw.y);
+    if (lane == 0) {
+      coef4 c; c.vr = s0; c.vi = s1; c.wr = s2; c.wi = s3;
+      out[(int64_t)i * a.nblk + blockIdx.x] = c;
+    }
+  }
+}
+
+// First pass: alpha from the matvec partials, y -= alpha v_j, b0 partials, then the dot products.
+template <typename R>
+__global__ void __launch_bounds__(kGsThreads)
+gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_part) {
+  using C = cplx<R>;
+  __shared__ double sh[32];
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < n_alpha_part; i += kGsThreads) {
+    ar += alpha_part[i].x;
+    ai += alpha_part[i].y;
+  }
+  ar = block_sum(ar, sh);
+  ai = block_sum(ai, sh);
+  const int j = a.j;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.T[(int64_t)j * a.ldt + j] = ar;                 // t_{j,j} (its real part)
+    StepState* st = a.st;
+    st->alpha_im = ai;
+    st->done = 0;
+    double tm = fmax(st->tmax, fabs(ar));
+    if (j > 0) tm = fmax(tm, fabs(a.T[(int64_t)j * a.ldt + j - 1]));
+    st->tmax = tm;
+    st->n_passes += 1;
+    st->units_first += (double)(j + 1) * (double)a.h;
+  }
+  const R alpha = (R)ar;
+  const C* vj = (const C*)a.V + (int64_t)j * a.n;
+  C* y = (C*)a.y;
+  const int64_t h = a.h;
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+  double nrm = 0.0;
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kGsThreads) {
+    C y1 = y[p], y2 = y[h + p];
+    const C v1 = vj[p], v2 = vj[h + p];
+    y1.x -= alpha * v1.x; y1.y -= alpha * v1.y;
+    y2.x -= alpha * v2.x; y2.y -= alpha * v2.y;
+    y[p] = y1;
+    y[h + p] = y2;
+    nrm += cabs2(y1) + cabs2(y2);
+  }
+  nrm = block_sum(nrm, sh);  // its barriers also publish the y writes to the whole block
+  if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
+  dot_body<R>(a, p0, p1);
+}
+
+// Later passes: first finish the test of the previous pass, then the dot products.
+template <typename R>
+__global__ void __launch_bounds__(kGsThreads) gs_dot_kernel(GSArgs a, int pass) {
+  __shared__ double sh[32];
+  __shared__ int s_skip;
+  StepState* st = a.st;
+  if (threadIdx.x == 0) s_skip = st->done;
+  __syncthreads();
+  if (s_skip) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < a.nblk; b += kGsThreads) s += a.part_nrm[b];
+  const double nrm_prev = sqrt(block_sum(s, sh));   // b1 after pass - 1
+  const double ref = st->nrm[pass - 2];              // b0 before pass - 1
+  if (kSqrt2 * nrm_prev > ref) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->nrm[pass - 1] = nrm_prev;
+      st->beta = nrm_prev;
+      st->done = 1;
+    }
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->nrm[pass - 1] = nrm_prev;
+    st->n_passes += 1;
+    st->units_dot += (double)(a.j + 1) * (double)a.h;
+  }
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, a.h);
+  dot_body<R>(a, p0, p1);
+}
+
+// Reduce the dot partials of every column (one block per column); with `first`, block j+1 also
+// reduces b0.
+__global__ void __launch_bounds__(kRedThreads) gs_reduce_kernel(GSArgs a, int first) {
+  __shared__ double sh[32];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = first ? 0 : a.st->done;
+  __syncthreads();
+  if (s_skip) return;
+  const int col = blockIdx.x;
+  if (col <= a.j) {
+    const coef4* src = (const coef4*)a.part_dot + (int64_t)col * a.nblk;
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int b = threadIdx.x; b < a.nblk; b += kRedThreads) {
+      const coef4 c = src[b];
+      s0 += c.vr; s1 += c.vi; s2 += c.wr; s3 += c.wi;
+    }
+    s0 = block_sum(s0, sh); s1 = block_sum(s1, sh); s2 = block_sum(s2, sh); s3 = block_sum(s3, sh);
+    if (threadIdx.x == 0) {
+      coef4 c; c.vr = s0; c.vi = s1; c.wr = s2; c.wi = s3;
+      a.coef[col] = c;
+    }
+  } else {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < a.nblk; b += kRedThreads) s += a.part_nrm[b];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) a.st->nrm[0] = sqrt(s);
+  }
+}
+
+// y -= V c_v + W c_w over this block's rows; partial ||y||^2.
+template <typename R>
+__global__ void __launch_bounds__(kGsThreads) gs_update_kernel(GSArgs a) {
+  using C = cplx<R>;
+  extern __shared__ coef4 sc[];
+  __shared__ C red1[kColGroups][32], red2[kColGroups][32];
+  __shared__ double sh[32];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = a.st->done;
+  __syncthreads();
+  if (s_skip) return;
+  const int j = a.j;
+  for (int i = threadIdx.x; i <= j; i += kGsThreads) sc[i] = a.coef[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.st->units_update += (double)(j + 1) * (double)a.h;
+  __syncthreads();
+  const C* V = (const C*)a.V;
+  C* y = (C*)a.y;
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int64_t n = a.n, h = a.h;
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+  double nrm = 0.0;
+  for (int64_t pb = p0; pb < p1; pb += 32) {
+    const int64_t p = pb + lane;
+    const bool ok = p < p1;
+    C acc1 = mk<R>(0, 0), acc2 = mk<R>(0, 0);
+    if (ok) {
+      for (int i = q; i <= j; i += kColGroups) {
+        const C* vi = V + (int64_t)i * n;
+        const C v1 = vi[p], v2 = vi[h + p];
+        const C cv = mk<R>((R)sc[i].vr, (R)sc[i].vi);
+        const C cw = mk<R>((R)sc[i].wr, (R)sc[i].wi);
+        const C ncw = mk<R>(-cw.x, -cw.y);
+        acc1 = cfma(v1, cv, acc1);      //  v1 c_v
+        acc1 = cfmac(v2, ncw, acc1);    // -conj(v2) c_w
+        acc2 = cfma(v2, cv, acc2);      //  v2 c_v
+        acc2 = cfmac(v1, cw, acc2);     // +conj(v1) c_w
+      }
+    }
+    red1[q][lane] = acc1;
+    red2[q][lane] = acc2;
+    __syncthreads();
+    if (q == 0 && ok) {
+      C s1 = red1[0][lane], s2 = red2[0][lane];
+#pragma unroll
+      for (int g = 1; g < kColGroups; ++g) { s1 = cadd(s1, red1[g][lane]); s2 = cadd(s2, red2[g][lane]); }
+      const C y1 = csub(y[p], s1), y2 = csub(y[h + p], s2);
+      y[p] = y1;
+      y[h + p] = y2;
+      nrm += cabs2(y1) + cabs2(y2);
+    }
+    __syncthreads();
+  }
+  nrm = block_sum(nrm, sh);
+  if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
+}
+
+// v_{j+1} = y / beta; t_{j+1,j} = beta; breakdown check.
+template <typename R>
+__global__ void __launch_bounds__(kGsThreads) gs_normalize_kernel(GSArgs a) {
+  using C = cplx<R>;
+  __shared__ double sh[32];
+  StepState* st = a.st;
+  const int done = st->done;
+  double beta;
+  if (done) {
+    beta = st->beta;
+  } else {  // the pass cap was reached: keep the norm after the last pass
+    double s = 0.0;
+    for (int b = threadIdx.x; b < a.nblk; b += kGsThreads) s += a.part_nrm[b];
+    beta = sqrt(block_sum(s, sh));
+  }
+  const double tmax = st->tmax;
+  const bool brk = !(beta > 1e-14 * fmax(tmax, 1.0));
+  const R inv = brk ? (R)0 : (R)(1.0 / beta);
+  const C* y = (const C*)a.y;
+  C* v = (C*)a.V + (int64_t)(a.j + 1) * a.n;
+  const int64_t h = a.h;
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kGsThreads) {
+    v[p] = cscale(y[p], inv);
+    v[h + p] = cscale(y[h + p], inv);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int j = a.j;
+    a.T[(int64_t)(j + 1) * a.ldt + j] = beta;        // t_{j+1,j}
+    if (j + 1 < a.m) a.T[(int64_t)j * a.ldt + j + 1] = beta;
+    if (brk) st->status = 5;
+  }
+}
+
+template <typename R>
+__global__ void fill_ones_kernel(cplx<R>* v, int64_t n, R val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = mk<R>(val, (R)0);
+}
+
+template <typename R>
+__global__ void fill_random_kernel(cplx<R>* v, int64_t n, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = mk<R>((R)u01_sym(seed + 2 * (uint64_t)i), (R)u01_sym(seed + 2 * (uint64_t)i + 1));
+}
+
+template <typename R>
+__global__ void sumsq_kernel(const cplx<R>* v, int64_t n, double* part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += cabs2(v[i]);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename R>
+__global__ void scale_by_norm_kernel(cplx<R>* v, int64_t n, const double* part, int nblk) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+  s = block_sum(s, sh);
+  const R inv = (R)(1.0 / sqrt(s));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = cscale(v[i], inv);
+}
+
+template <typename R>
+__global__ void jsym_check_kernel(const cplx<R>* v, const cplx<R>* y, int64_t h, double* out) {
+  __shared__ double sh[32];
+  double wr = 0, wi = 0, yy = 0, vv = 0;
+  for (int64_t p = threadIdx.x; p < h; p += blockDim.x) {
+    const cplx<R> v1 = v[p], v2 = v[h + p], y1 = y[p], y2 = y[h + p];
+    // w^H y with w = J v^*: sum (v1 y2 - v2 y1)
+    wr += (double)v1.x * y2.x - (double)v1.y * y2.y - ((double)v2.x * y1.x - (double)v2.y * y1.y);
+    wi += (double)v1.x * y2.y + (double)v1.y * y2.x - ((double)v2.x * y1.y + (double)v2.y * y1.x);
+    yy += cabs2(y1) + cabs2(y2);
+    vv += cabs2(v1) + cabs2(v2);
+  }
+  wr = block_sum(wr, sh); wi = block_sum(wi, sh); yy = block_sum(yy, sh); vv = block_sum(vv, sh);
+  if (threadIdx.x == 0) { out[0] = wr; out[1] = wi; out[2] = yy; out[3] = vv; }
+}
+
+}  // namespace
+
+int gs_blocks(int64_t h, int* rows_per_block) {
+  const int64_t tiles = (h + 31) / 32;
+  const int64_t target = 4 * 152;
+  const int64_t tpb = (tiles + target - 1) / target;
+  const int rpb = (int)(32 * (tpb < 1 ? 1 : tpb));
+  if (rows_per_block) *rows_per_block = rpb;
+  return (int)((h + rpb - 1) / rpb);
+}
+
+template <typename R>
+cudaError_t launch_gs_first(const GSArgs& a, const double2* alpha_part, int n_alpha_part, cudaStream_t s) {
+  gs_first_kernel<R><<<a.nblk, kGsThreads, 0, s>>>(a, alpha_part, n_alpha_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_reduce(const GSArgs& a, int first, cudaStream_t s) {
+  gs_reduce_kernel<<<a.j + 1 + (first ? 1 : 0), kRedThreads, 0, s>>>(a, first);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gs_update(const GSArgs& a, cudaStream_t s) {
+  gs_update_kernel<R><<<a.nblk, kGsThreads, (size_t)(a.j + 1) * sizeof(coef4), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gs_dot(const GSArgs& a, int pass, cudaStream_t s) {
+  gs_dot_kernel<R><<<a.nblk, kGsThreads, 0, s>>>(a, pass);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gs_normalize(const GSArgs& a, cudaStream_t s) {
+  gs_normalize_kernel<R><<<a.nblk, kGsThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fill_ones(void* v, int64_t n, cudaStream_t s) {
+  fill_ones_kernel<R><<<256, 256, 0, s>>>((cplx<R>*)v, n, (R)(1.0 / sqrt((double)n)));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fill_random(void* v, int64_t n, uint64_t seed, cudaStream_t s) {
+  fill_random_kernel<R><<<256, 256, 0, s>>>((cplx<R>*)v, n, seed);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_normalize_col(void* v, int64_t n, double* part, int nblk, cudaStream_t s) {
+  sumsq_kernel<R><<<nblk, 256, 0, s>>>((const cplx<R>*)v, n, part);
+  scale_by_norm_kernel<R><<<nblk, 256, 0, s>>>((cplx<R>*)v, n, part, nblk);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_jsym_check(const void* v, const void* y, int64_t h, double* out, cudaStream_t s) {
+  jsym_check_kernel<R><<<1, 1024, 0, s>>>((const cplx<R>*)v, (const cplx<R>*)y, h, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gs_first<double>(const GSArgs&, const double2*, int, cudaStream_t);
+template cudaError_t launch_gs_update<double>(const GSArgs&, cudaStream_t);
+template cudaError_t launch_gs_dot<double>(const GSArgs&, int, cudaStream_t);
+template cudaError_t launch_gs_normalize<double>(const GSArgs&, cudaStream_t);
+template cudaError_t launch_fill_ones<double>(void*, int64_t, cudaStream_t);
+template cudaError_t launch_fill_random<double>(void*, int64_t, uint64_t, cudaStream_t);
+template cudaError_t launch_normalize_col<double>(void*, int64_t, double*, int, cudaStream_t);
+template cudaError_t launch_jsym_check<double>(const void*, const void*, int64_t, double*, cudaStream_t);
+
+}  // namespace jtr

@@ -1,0 +1,107 @@
+// internal.h -- host-side launchers shared between the translation units of libjtrlan.
+// Not part of the public ABI (that is include/jtrlan.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace jtr {
+
+// Description of the operator as the kernels see it (device pointers owned by the context).
+struct OpDev {
+  int kind;            // JTRLAN_DENSE / JTRLAN_STENCIL4D
+  int64_t n;           // vector length
+  int64_t h;           // n / 2
+  int dims[4];
+  int64_t vol;
+  double m0, kappa;
+  const void* a11;     // dense blocks (h x h row-major), working precision
+  const void* a12;
+  const void* U;       // stencil links [4][V][9], working precision
+  const void* W;
+};
+
+// Modes of the matvec kernels.
+enum MvMode { MV_PLAIN = 0, MV_ALPHA = 1, MV_RESID = 2 };
+
+// y = A x.  MV_ALPHA also writes per-block partial sums of x^H y to part (double2[nblk]).
+// MV_RESID takes ncand columns x_c = X[:, cand[c]] (ld = n), computes ||A x_c - lam[c] x_c||^2
+// per block into part[c * nblk + b] (double) and writes no y.  Returns the per-column block
+// count (nblk) through *nblk_out.
+template <typename R>
+cudaError_t launch_matvec(const OpDev& op, const cplx<R>* x, cplx<R>* y, MvMode mode, double* part,
+                          const int* cand, const double* lam, int ncand, int64_t ldx,
+                          int* nblk_out, cudaStream_t s);
+int matvec_blocks(const OpDev& op);  // nblk of launch_matvec for one column
+
+// Lanczos-step Gram-Schmidt against [V, W] with W = J V^* implicit (Algorithm 2).
+struct GSArgs {
+  const void* V;       // n x (m+1) complex, ld = n, working precision
+  int64_t n, h;
+  void* y;             // the vector being orthogonalised (n complex)
+  int j;               // current column: v_j = V[:, j]; columns 0..j take part
+  double* part_dot;    // [(m+1)][nblk] coef4 partials
+  double* part_nrm;    // [nblk] partial squared norms
+  coef4* coef;         // [(m+1)] reduced coefficients
+  StepState* st;
+  double* T;           // T-bar, (m+1) x (m+1) row-major
+  int ldt;             // m + 1
+  int m;
+  int nblk;            // blocks of the row-parallel GS kernels
+  int rows_per_block;  // row pairs per block (multiple of 32)
+};
+int gs_blocks(int64_t h, int* rows_per_block);
+
+// The kernels of one Lanczos step's reorthogonalisation, in launch order:
+//   first, reduce(first=1), update, {dot(pass), reduce(0), update} for pass = 2..P, normalize.
+template <typename R>
+cudaError_t launch_gs_first(const GSArgs& a, const double2* alpha_part, int n_alpha_part, cudaStream_t s);
+cudaError_t launch_gs_reduce(const GSArgs& a, int first, cudaStream_t s);
+template <typename R>
+cudaError_t launch_gs_update(const GSArgs& a, cudaStream_t s);
+template <typename R>
+cudaError_t launch_gs_dot(const GSArgs& a, int pass, cudaStream_t s);
+template <typename R>
+cudaError_t launch_gs_normalize(const GSArgs& a, cudaStream_t s);
+
+// Kernel classes for the optional per-kernel profile.
+enum KernelTag {
+  K_MATVEC = 0, K_GS_FIRST, K_GS_REDUCE, K_GS_UPDATE, K_GS_DOT, K_GS_NORMALIZE, K_RITZ, K_ROTATE,
+  K_RESID, K_SHRINK, K_OTHER, K_NTAGS
+};
+template <typename R>
+cudaError_t launch_fill_ones(void* v, int64_t n, cudaStream_t s);
+template <typename R>
+cudaError_t launch_normalize_col(void* v, int64_t n, double* part, int nblk, cudaStream_t s);
+
+// Ritz solve of the leading m x m block of T-bar (FP64, one CTA): eigenvalues sorted toward
+// the wanted end into lam[m], eigenvectors into Z (m x m column-major), work >= 2*mp*mp doubles.
+cudaError_t launch_ritz(const double* T, int ldt, int m, int which, double* lam, double* Z,
+                        double* work, cudaStream_t s);
+
+// Vout[:, 0:kk] = V[:, 0:m] * Z[:, 0:kk] (V complex n x m, ld n; Z real m x kk, ld m).
+template <typename R>
+cudaError_t launch_rotate(const void* V, int64_t n, int m, const double* Z, int kk, void* Vout,
+                          cudaStream_t s);
+// V[:, c] = Vsrc[:, perm[c]] for c < k and V[:, k] = V[:, m] (restart shrink, Algorithm 1).
+template <typename R>
+cudaError_t launch_shrink(void* V, const void* Vsrc, int64_t n, const int* perm, int k, int m,
+                          cudaStream_t s);
+// out[:, c] = V[:, order[c]] and, if partners, out[:, nev + c] = J conj(V[:, order[c]]).
+template <typename R>
+cudaError_t launch_gather_pairs(const void* V, int64_t n, const int* order, int nev, int partners,
+                                void* out, cudaStream_t s);
+// Column sums of squares partials -> sqrt into out[c] (c < ncol), partials [ncol][nblk].
+cudaError_t launch_reduce_norms(const double* part, int nblk, int ncol, double* out, cudaStream_t s);
+// Lemma 1 check partials: sum (v1 y2 - v2 y1), ||y||^2, ||v||^2 over all rows -> out[4].
+template <typename R>
+cudaError_t launch_jsym_check(const void* v, const void* y, int64_t h, double* out, cudaStream_t s);
+template <typename R>
+cudaError_t launch_fill_random(void* v, int64_t n, uint64_t seed, cudaStream_t s);
+// Gathers lam[0..m), Z[m-1, 0..m), T[m][m-1], st->status into rep[2m + 2].
+cudaError_t launch_report(const double* lam, const double* Z, int m, const double* T, int ldt,
+                          const StepState* st, double* rep, cudaStream_t s);
+
+}  // namespace jtr

@@ -1,0 +1,88 @@
+"""Convenience layer over the C ABI for PyTorch users: uploads arrays, calls jtrlan_create /
+jtrlan_solve / jtrlan_pairs, and returns torch tensors.  Marshalling only; the solve runs in
+libjtrlan's kernels on the current CUDA stream."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def _dev(a, device):
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=torch.complex128).contiguous()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).to(device)
+
+
+class JTRLan:
+    """One operator + parameter set bound to a library context on ``device``.
+
+    ``kind`` is "stencil" (U, W of shape (4, V, 3, 3), dims, m0, kappa) or "dense" (A11, A12).
+    """
+
+    def __init__(self, kind, *, nev, m, mwin, tol, which="smallest", dims=None, m0=None, kappa=None,
+                 U=None, W=None, A11=None, A12=None, v1=None, max_restarts=0, gs_max_passes=0,
+                 check_jsym=False, profile=False, device="cuda"):
+        B.load()
+        self.device = torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device)
+        keep = []
+        if kind == "stencil":
+            Ud, Wd = _dev(U, self.device), _dev(W, self.device)
+            keep += [Ud, Wd]
+            op = B.stencil_operator(dims, m0, kappa, Ud.data_ptr(), Wd.data_ptr())
+        elif kind == "dense":
+            Ad, Bd = _dev(A11, self.device), _dev(A12, self.device)
+            keep += [Ad, Bd]
+            op = B.dense_operator(2 * Ad.shape[0], Ad.data_ptr(), Bd.data_ptr())
+        else:
+            raise ValueError(kind)
+        self.n = int(op.n)
+        self.nev = int(nev)
+        v1p = None
+        if v1 is not None:
+            v1d = _dev(v1, self.device)
+            keep.append(v1d)
+            v1p = v1d.data_ptr()
+        w = B.JTRLAN_LARGEST if which == "largest" else B.JTRLAN_SMALLEST
+        self._keep_v1 = keep[-1] if v1 is not None else None
+        prm = B.params(nev, m, mwin, tol, which=w, max_restarts=max_restarts,
+                       gs_max_passes=gs_max_passes, v1_ptr=v1p, check_jsym=int(check_jsym),
+                       profile=int(profile))
+        self.ctx = B.jtrlan_create(op, prm, self.stream.cuda_stream)
+        # jtrlan_create copied the operator; v1 is read at solve time, so it is kept alive.
+
+    def apply(self, x: torch.Tensor) -> torch.Tensor:
+        x = _dev(x, self.device)
+        y = torch.empty_like(x)
+        B.jtrlan_apply(self.ctx, x.data_ptr(), y.data_ptr())
+        return y
+
+    def solve(self) -> dict:
+        return B.jtrlan_solve(self.ctx)
+
+    def pairs(self, with_partners=False):
+        ev = np.zeros(self.nev)
+        res = np.zeros(self.nev)
+        ncol = 2 * self.nev if with_partners else self.nev
+        X = torch.empty((ncol, self.n), dtype=torch.complex128, device=self.device)
+        B.jtrlan_pairs(self.ctx, int(with_partners), ev.ctypes.data_as(ctypes.c_void_p),
+                       ctypes.c_void_p(X.data_ptr()), res.ctypes.data_as(ctypes.c_void_p))
+        return ev, X.T, res   # X.T is n x ncol (column-major storage)
+
+    def profile(self) -> dict:
+        return B.jtrlan_get_profile(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            B.jtrlan_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

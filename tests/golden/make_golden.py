@@ -34,6 +34,12 @@ def stencil_golden(name, tol=1e-12):
                evals=[float(v) for v in out["evals"]], res=[float(v) for v in out["res"]],
                n_matvec=out["n_matvec"], n_restarts=out["n_restarts"],
                oracle_seconds=round(time.time() - t0, 1))
+    # the same solve at the benchmark tolerance 1e-8: its outer-iteration count scales the
+    # benchmark's bounded CPU-oracle sample to a whole solve
+    t0 = time.time()
+    out8 = tj.trlan_jsym(mv, n, w["nev"], w["m"], w["mwin"], 1e-8)
+    rec["tol_1e-8"] = dict(n_matvec=out8["n_matvec"], n_restarts=out8["n_restarts"],
+                           evals=[float(v) for v in out8["evals"]], oracle_seconds=round(time.time() - t0, 1))
     with open(os.path.join(HERE, f"{name}.json"), "w") as f:
         json.dump(rec, f, indent=1)
     print(name, rec["n_matvec"], rec["n_restarts"], rec["oracle_seconds"])

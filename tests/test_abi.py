@@ -1,0 +1,113 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads, exports every
+function include/jtrlan.h declares, the ctypes structs match the C layout, and invalid arguments
+are rejected before any CUDA work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2001_07428_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "jtrlan.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(B.LIB_PATH):
+        from paper_2001_07428_gb300 import build
+        build.build()
+    return B.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(jtrlan_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    assert {"jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs"} <= set(declared_functions())
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (jtrlan_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "jtrlan.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_operator), offsetof(jtrlan_operator, n),
+         offsetof(jtrlan_operator, m0), offsetof(jtrlan_operator, a11), offsetof(jtrlan_operator, W));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_params), offsetof(jtrlan_params, tol),
+         offsetof(jtrlan_params, v1), offsetof(jtrlan_params, check_jsym), offsetof(jtrlan_params, profile));
+  printf("%zu %zu %zu %zu\n", sizeof(jtrlan_stats), offsetof(jtrlan_stats, n_restarts),
+         offsetof(jtrlan_stats, solve_ms), offsetof(jtrlan_stats, n_launches));
+  printf("%zu %zu %zu %zu\n", sizeof(jtrlan_profile), offsetof(jtrlan_profile, ms),
+         offsetof(jtrlan_profile, launches), offsetof(jtrlan_profile, work));
+  return 0;
+}''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [list(map(int, l.split())) for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines()]
+    O, P, S, F = B.jtrlan_operator, B.jtrlan_params, B.jtrlan_stats, B.jtrlan_profile
+    assert got[0] == [ctypes.sizeof(O), O.n.offset, O.m0.offset, O.a11.offset, O.W.offset]
+    assert got[1] == [ctypes.sizeof(P), P.tol.offset, P.v1.offset, P.check_jsym.offset, P.profile.offset]
+    assert got[2] == [ctypes.sizeof(S), S.n_restarts.offset, S.solve_ms.offset, S.n_launches.offset]
+    assert got[3] == [ctypes.sizeof(F), F.ms.offset, F.launches.offset, F.work.offset]
+
+
+def test_status_strings(lib):
+    for s in range(9):
+        assert lib.jtrlan_status_string(s)
+
+
+DUMMY = 0x1000  # never dereferenced: validation fails before any copy
+
+
+@pytest.mark.parametrize("case", ["odd_n", "stencil_n", "nev_ge_m", "m_ge_half", "neg_mwin", "tol",
+                                  "which", "null_links", "kind", "precision"])
+def test_invalid_arguments_rejected_without_gpu(lib, case):
+    op = B.stencil_operator((4, 4, 4, 4), 8.5, 0.3, DUMMY, DUMMY)
+    prm = B.params(6, 24, 12, 1e-10)
+    if case == "odd_n":
+        op = B.dense_operator(201, DUMMY, DUMMY)
+    elif case == "stencil_n":
+        op.n = op.n + 2
+    elif case == "nev_ge_m":
+        prm.nev = 24
+    elif case == "m_ge_half":
+        prm.m = op.n // 2
+    elif case == "neg_mwin":
+        prm.mwin = -1
+    elif case == "tol":
+        prm.tol = 0.0
+    elif case == "which":
+        prm.which = 7
+    elif case == "null_links":
+        op.U = None
+    elif case == "kind":
+        op.kind = 9
+    elif case == "precision":
+        prm.precision = 5
+    with pytest.raises(B.JTRLanError) as ei:
+        B.jtrlan_create(op, prm, 0)
+    assert ei.value.status == B.JTRLAN_EINVAL
+
+
+def test_null_context_calls(lib):
+    assert lib.jtrlan_solve(None, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_pairs(None, 0, None, None, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_apply(None, None, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_get_profile(None, None) == B.JTRLAN_EINVAL
+    lib.jtrlan_destroy(None)
