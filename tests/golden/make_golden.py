@@ -39,6 +39,7 @@ def stencil_golden(name, tol=1e-12):
     t0 = time.time()
     out8 = tj.trlan_jsym(mv, n, w["nev"], w["m"], w["mwin"], 1e-8)
     rec["tol_1e-8"] = dict(n_matvec=out8["n_matvec"], n_restarts=out8["n_restarts"],
+                           n_resid_matvec=out8["n_resid_matvec"],
                            evals=[float(v) for v in out8["evals"]], oracle_seconds=round(time.time() - t0, 1))
     with open(os.path.join(HERE, f"{name}.json"), "w") as f:
         json.dump(rec, f, indent=1)
