@@ -171,6 +171,35 @@ jtrlan_status jtrlan_get_profile(jtrlan_ctx* ctx, jtrlan_profile* out);
 /* Frees everything the context owns (after synchronising its stream).  NULL is a no-op. */
 void jtrlan_destroy(jtrlan_ctx* ctx);
 
+/* Residual norms without device allocation.
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot call cudaMalloc --
+ * an application whose own caching allocator already holds the device memory it may use, code
+ * that must not let cudaMalloc's implicit synchronisation stall other streams, or a plug-in given
+ * no allocation rights.  It computes res[i] = ||A x_i - lambda[i] x_i|| (the true residual that
+ * Algorithm 1 tests) for the ncols columns x_i of X, with the same kernels as the solver's
+ * convergence check, and allocates nothing: its scratch lives in one static device array of
+ * 8 * JTRLAN_NOALLOC_MAX_PARTIALS + 20 * JTRLAN_NOALLOC_MAX_COLS bytes (about 2 MiB) that every GPU
+ * which loads the library holds until the process exits.
+ *   op: the operator; dtype must be JTRLAN_C128 and a11/a12 or U/W must be DEVICE pointers (no
+ *     copy or conversion is made).  X: device, n x ncols complex128, column-major with leading
+ *     dimension ldx >= n.  lambda: host, ncols doubles.  res: host, ncols doubles (written).
+ *   cuda_stream: the stream to run on (NULL = legacy default); the call synchronises it.
+ * Limits: ncols <= JTRLAN_NOALLOC_MAX_COLS and ncols * B <= JTRLAN_NOALLOC_MAX_PARTIALS, where B is
+ *   the number of blocks of one product (stencil: ceil(24 V / 256); dense: ceil((n/2) / 8)).
+ *   Larger requests fail with JTRLAN_EINVAL and a message naming the limit: split the columns.
+ * The first call on a device looks up the array's device address there (cudaGetSymbolAddress with
+ * that device current); make that first call before any stream capture on the device.
+ * All calls on a device share the one array, and every call overwrites all of it that it reads,
+ * so nothing carries over between calls; calls whose GPU work overlaps (on different streams or
+ * host threads) race on it and must be serialised by the caller.
+ * Errors: JTRLAN_EINVAL (null pointers, sizes beyond the limits, unsupported dtype), JTRLAN_ECUDA. */
+#define JTRLAN_NOALLOC_MAX_PARTIALS 262144
+#define JTRLAN_NOALLOC_MAX_COLS 1024
+jtrlan_status jtrlan_residual_norms_noalloc(const jtrlan_operator* op, const void* X, int64_t ldx,
+                                            int ncols, const double* lambda, double* res,
+                                            void* cuda_stream);
+
 /* Static text for a status code. */
 const char* jtrlan_status_string(jtrlan_status s);
 

@@ -21,7 +21,9 @@ JTRLAN_SMALLEST, JTRLAN_LARGEST = 0, 1
 JTRLAN_FP64, JTRLAN_MIXED = 0, 1
 
 EXPORTED = ["jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
-            "jtrlan_destroy", "jtrlan_status_string", "jtrlan_last_error"]
+            "jtrlan_residual_norms_noalloc", "jtrlan_destroy", "jtrlan_status_string", "jtrlan_last_error"]
+NOALLOC_MAX_PARTIALS = 262144   # JTRLAN_NOALLOC_MAX_PARTIALS
+NOALLOC_MAX_COLS = 1024         # JTRLAN_NOALLOC_MAX_COLS
 
 
 class jtrlan_operator(ctypes.Structure):
@@ -87,13 +89,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jtrlan_pairs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p]
     lib.jtrlan_get_profile.argtypes = [ctypes.c_void_p, P(jtrlan_profile)]
+    lib.jtrlan_residual_norms_noalloc.argtypes = [P(jtrlan_operator), ctypes.c_void_p, ctypes.c_int64,
+                                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p]
     lib.jtrlan_destroy.argtypes = [ctypes.c_void_p]
     lib.jtrlan_destroy.restype = None
     lib.jtrlan_status_string.argtypes = [ctypes.c_int]
     lib.jtrlan_status_string.restype = ctypes.c_char_p
     lib.jtrlan_last_error.argtypes = []
     lib.jtrlan_last_error.restype = ctypes.c_char_p
-    for f in ("jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile"):
+    for f in ("jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
+              "jtrlan_residual_norms_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -132,6 +138,14 @@ def jtrlan_get_profile(ctx) -> dict:
     pr = jtrlan_profile()
     _check(load().jtrlan_get_profile(ctx, ctypes.byref(pr)))
     return pr.as_dict()
+
+
+def jtrlan_residual_norms_noalloc(op: jtrlan_operator, x_ptr: int, ldx: int, ncols: int, lambda_ptr,
+                                  res_ptr, stream: int = 0):
+    """||A x_i - lambda_i x_i|| for the columns of a device array, without any device allocation
+    (for callers that cannot allocate device memory; see include/jtrlan.h)."""
+    _check(load().jtrlan_residual_norms_noalloc(ctypes.byref(op), ctypes.c_void_p(x_ptr), int(ldx), int(ncols),
+                                                lambda_ptr, res_ptr, ctypes.c_void_p(stream)))
 
 
 def jtrlan_destroy(ctx):

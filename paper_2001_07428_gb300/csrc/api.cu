@@ -19,6 +19,12 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+void jtr::set_last_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+
 jtrlan_status fail(jtrlan_status s, const std::string& msg) {
   g_last_error = msg;
   return s;

@@ -104,4 +104,7 @@ cudaError_t launch_fill_random(void* v, int64_t n, uint64_t seed, cudaStream_t s
 cudaError_t launch_report(const double* lam, const double* Z, int m, const double* T, int ldt,
                           const StepState* st, double* rep, cudaStream_t s);
 
+// Sets the thread-local text returned by jtrlan_last_error().
+void set_last_error(const char* msg);
+
 }  // namespace jtr
