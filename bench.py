@@ -315,7 +315,7 @@ def run_gb300(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": t_mean * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args.workload, w),
             "solve_stats": {k: stats[-1][k] for k in ("n_matvec", "n_resid_matvec", "n_gs_passes", "n_restarts",
-                                                       "icnv")},
+                                                       "icnv", "n_ritz_fallbacks")},
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "stencil_matvec": stencil,
             "kernels": kernels,
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}

@@ -116,6 +116,7 @@ typedef struct {
   int icnv;                /* converged pairs at exit */
   double solve_ms;         /* wall time of jtrlan_solve on the host clock */
   int64_t n_launches;      /* CUDA kernels launched by the solve */
+  int n_ritz_fallbacks;    /* restarts whose fast Ritz solve failed a check (Jacobi used) */
 } jtrlan_stats;
 
 /* Per-kernel-class profile of the last solve (filled when jtrlan_params.profile was set; the

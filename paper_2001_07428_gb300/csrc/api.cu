@@ -44,7 +44,7 @@ __global__ void c64_to_c128_kernel(const float2* in, double2* out, int64_t count
 }
 
 const char* kTagNames[K_NTAGS] = {"matvec", "gs_first", "gs_reduce", "gs_update", "gs_dot", "gs_normalize",
-                                  "ritz", "rotate", "resid", "shrink", "other"};
+                                  "ritz", "rotate", "resid", "shrink", "other", "ritz_fallback"};
 
 // Optional per-launch CUDA-event timing, harvested at the host synchronisation points.
 struct Profiler {
@@ -108,6 +108,7 @@ struct jtrlan_ctx {
   double* lam = nullptr;
   double* Z = nullptr;
   double* ritz_ws = nullptr;
+  int* ritz_flags = nullptr;
   double* work_ritz() { return ritz_ws; }
   double* part_dot = nullptr;
   double* part_nrm = nullptr;
@@ -267,6 +268,7 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));
   JT_TRY(c->dalloc(&c->Z, (size_t)m * m * sizeof(double)));
   JT_TRY(c->dalloc(&c->ritz_ws, (size_t)2 * mp * mp * sizeof(double)));
+  JT_TRY(c->dalloc(&c->ritz_flags, (size_t)(m + 1) * sizeof(int)));
   JT_TRY(c->dalloc(&c->part_dot, (size_t)(m + 1) * c->gs_nblk * sizeof(coef4)));
   JT_TRY(c->dalloc(&c->part_nrm, (size_t)c->gs_nblk * sizeof(double)));
   JT_TRY(c->dalloc(&c->coef, (size_t)(m + 1) * sizeof(coef4)));
@@ -278,7 +280,7 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   JT_TRY(c->dalloc(&c->d_cand, (size_t)c->nev * sizeof(int)));
   JT_TRY(c->dalloc(&c->d_perm, (size_t)m * sizeof(int)));
   JT_TRY(c->dalloc(&c->d_order, (size_t)c->nev * sizeof(int)));
-  JT_TRY(c->dalloc(&c->d_rep, (size_t)(2 * m + 8) * sizeof(double)));
+  JT_TRY(c->dalloc(&c->d_rep, (size_t)(2 * m + 8) * sizeof(double)));  // lam, z_m, 8 scalars
   JT_TRY(c->dalloc(&c->d_misc, 16 * sizeof(double)));
   JT_TRY(c->halloc(&c->h_rep, (size_t)(2 * m + 8) * sizeof(double)));
   JT_TRY(c->halloc(&c->h_T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
@@ -366,24 +368,29 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
     c->work[K_MATVEC] += (double)(m - k) * mv_units;
     stt.n_restarts += 1;
     // ---- Rayleigh-Ritz: T_m = Z Lambda Z^T, sorted; V_m Z into Vtmp
-    LAUNCH(K_RITZ, launch_ritz(c->T, ldt, m, c->prm.which, c->lam, c->Z, c->work_ritz(), s));
+    LAUNCH(K_RITZ, launch_ritz(c->T, ldt, m, k, c->kk, c->prm.which, c->lam, c->Z, c->ritz_flags, s));
+    c->nl[K_RITZ] += 1;  // two kernels: bisection + inverse iteration, checks
+    LAUNCH(K_RITZ_FALLBACK, launch_ritz_fallback(c->T, ldt, m, c->prm.which, c->lam, c->Z, c->work_ritz(),
+                                                 c->ritz_flags, &c->st->n_ritz_fallbacks, s));
     LAUNCH(K_ROTATE, launch_rotate<double>(c->V, n, m, c->Z, c->kk, c->Vtmp, s));
     c->work[K_ROTATE] += 2.0 * (double)n * m * c->kk;
     LAUNCH(K_OTHER, launch_report(c->lam, c->Z, m, c->T, ldt, c->st, c->d_rep, s));
-    JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * m + 7) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * m + 8) * sizeof(double), cudaMemcpyDeviceToHost, s));
     JT_CUDA(cudaStreamSynchronize(s));
     JT_CUDA(c->prof.harvest());
     stt.n_gs_passes = (int64_t)c->h_rep[2 * m + 2];
     c->work[K_GS_FIRST] = c->h_rep[2 * m + 4];
     c->work[K_GS_DOT] = c->h_rep[2 * m + 5];
     c->work[K_GS_UPDATE] = c->h_rep[2 * m + 6];
+    stt.n_ritz_fallbacks = (int)c->h_rep[2 * m + 7];
     if (c->h_rep[2 * m + 1] != 0.0) {
       c->stats = stt;
       if (stats_out) *stats_out = stt;
       return fail(JTRLAN_EBREAKDOWN, "Lanczos breakdown: beta below 1e-14 max|T|");
     }
     const double beta_m = c->h_rep[2 * m];
-    for (int i = 0; i < m; ++i) {
+    const int kk = c->kk;                     // Ritz pairs computed (nearest the wanted end)
+    for (int i = 0; i < kk; ++i) {
       lamv[i] = c->h_rep[i];
       arrow[i] = beta_m * c->h_rep[m + i];   // t_{m+1,i} = t_{m+1,m} z_{m,i}
     }
@@ -418,7 +425,7 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
     for (int i = 0; i < nev; ++i) if (!conv[i]) perm[w++] = i;
     for (int i = nev; i < m; ++i) perm[i] = i;
     std::vector<double> ev2(nev), res2(nev), lam2(m), arrow2(m);
-    for (int i = 0; i < m; ++i) { lam2[i] = lamv[perm[i]]; arrow2[i] = arrow[perm[i]]; }
+    for (int i = 0; i < kk; ++i) { lam2[i] = lamv[perm[i]]; arrow2[i] = arrow[perm[i]]; }
     for (int i = 0; i < nev; ++i) { ev2[i] = ev[perm[i]]; res2[i] = res[perm[i]]; }
     ev = ev2; res = res2; lamv = lam2; arrow = arrow2;
     for (int i = 0; i < icnv; ++i) arrow[i] = 0.0;   // decouple the converged subspace

@@ -74,6 +74,7 @@ struct StepState {
   double units_first;  // sum over steps of (j+1) * n/2: row pair x column products of the first dot
   double units_dot;    // the same for the dot of every executed later pass
   double units_update; // the same for every executed update pass
+  long long n_ritz_fallbacks;  // restarts whose Ritz fast path failed its checks (Jacobi used)
 };
 
 // Counter-based pseudo-random numbers (splitmix64, Steele, Lea & Flood 2014).

@@ -69,17 +69,27 @@ cudaError_t launch_gs_normalize(const GSArgs& a, cudaStream_t s);
 // Kernel classes for the optional per-kernel profile.
 enum KernelTag {
   K_MATVEC = 0, K_GS_FIRST, K_GS_REDUCE, K_GS_UPDATE, K_GS_DOT, K_GS_NORMALIZE, K_RITZ, K_ROTATE,
-  K_RESID, K_SHRINK, K_OTHER, K_NTAGS
+  K_RESID, K_SHRINK, K_OTHER, K_RITZ_FALLBACK, K_NTAGS
 };
 template <typename R>
 cudaError_t launch_fill_ones(void* v, int64_t n, cudaStream_t s);
 template <typename R>
 cudaError_t launch_normalize_col(void* v, int64_t n, double* part, int nblk, cudaStream_t s);
 
-// Ritz solve of the leading m x m block of T-bar (FP64, one CTA): eigenvalues sorted toward
-// the wanted end into lam[m], eigenvectors into Z (m x m column-major), work >= 2*mp*mp doubles.
-cudaError_t launch_ritz(const double* T, int ldt, int m, int which, double* lam, double* Z,
-                        double* work, cudaStream_t s);
+// Ritz solve of the leading m x m block of T-bar (FP64): the kk eigenpairs nearest the wanted
+// end, sorted toward it, into lam[0..kk) and Z[:, 0..kk) (m x m column-major, ld m).  k is the size
+// of the kept (arrow) part.  Fast path: bisection + inverse iteration, one warp per pair, checked;
+// on any failed check the one-CTA Jacobi kernel recomputes all m pairs.  flags >= kk + 1 ints,
+// work >= 2*mp*mp doubles (mp = m rounded up to even).  *nlaunch receives the kernel count.
+cudaError_t launch_ritz(const double* T, int ldt, int m, int k, int kk, int which, double* lam, double* Z,
+                        int* flags, cudaStream_t s);
+// The Jacobi fallback after launch_ritz: runs only if launch_ritz's checks failed (flags[0] != 0),
+// and then counts the event in *fallbacks.
+cudaError_t launch_ritz_fallback(const double* T, int ldt, int m, int which, double* lam, double* Z, double* work,
+                                 const int* flags, long long* fallbacks, cudaStream_t s);
+// The Jacobi kernel alone (all m pairs).
+cudaError_t launch_ritz_jacobi(const double* T, int ldt, int m, int which, double* lam, double* Z, double* work,
+                               cudaStream_t s);
 
 // Vout[:, 0:kk] = V[:, 0:m] * Z[:, 0:kk] (V complex n x m, ld n; Z real m x kk, ld m).
 template <typename R>
