@@ -151,6 +151,50 @@ def cpu_baseline(name, full_products, restarts=4):
                       f"products A v, {d['seconds']:.1f} s), scaled by the product count"}
 
 
+# ---------------------------------------------------------------- FP32 stencil matvec vs HBM
+STENCIL_LATTICES = {"16x16x16x16": (16, 16, 16, 16), "24x24x24x48": (24, 24, 24, 48)}
+
+
+def stencil_apply_roofline(dims, reps=20, seed=4):
+    """Times jtrlan_apply of the FP32 operator (a mixed-precision context, complex64 links) on the
+    seeded lattice `dims`: median device time over `reps` launches, L2 flushed before each, and the
+    algorithmic 84 complex64 words per site (72 link + 6 in + 6 out) per launch over that time."""
+    import torch
+
+    from paper_2001_07428_gb300 import binding as B
+    dev = torch.device("cuda", torch.cuda.current_device())
+    U, W = inputs.stencil_links(dims, seed)
+    vol = inputs.lattice_volume(dims)
+    n = 6 * vol
+    Ud = torch.from_numpy(U.astype(np.complex64)).to(dev)
+    Wd = torch.from_numpy(W.astype(np.complex64)).to(dev)
+    del U, W
+    stream = torch.cuda.current_stream(dev)
+    op = B.stencil_operator(dims, 8.5, 0.3, Ud.data_ptr(), Wd.data_ptr(), dtype=B.JTRLAN_C64)
+    ctx = B.jtrlan_create(op, B.params(1, 2, 1, TOL, precision=B.JTRLAN_MIXED), stream.cuda_stream)
+    x = torch.from_numpy(inputs.random_vector(n, seed).astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        B.jtrlan_apply(ctx, x.data_ptr(), y.data_ptr())
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.jtrlan_apply(ctx, x.data_ptr(), y.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    B.jtrlan_destroy(ctx)
+    t = statistics.median(ts)
+    hbm, src = measured_peaks()
+    algo = 84 * 8 * vol
+    gbs = algo / t / 1e9
+    return {"lattice": list(dims), "us": round(t * 1e6, 2), "algorithmic_bytes": algo, "gbs": round(gbs, 1),
+            "frac_of_hbm": round(gbs / hbm, 4), "hbm_peak_gbs": hbm, "peak_source": src}
+
+
 # ---------------------------------------------------------------- the reference arm (the oracle)
 def run_reference(args, rank, world):
     if rank != 0:
@@ -319,6 +363,7 @@ def run_gb300(args, rank, world, local_rank):
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "stencil_matvec": stencil,
             "kernels": kernels,
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
+    line["stencil_fp32"] = {k: stencil_apply_roofline(v) for k, v in STENCIL_LATTICES.items()}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, stats[-1]["n_matvec"] + stats[-1]["n_resid_matvec"])
     print(json.dumps(line), flush=True)
@@ -332,6 +377,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="stencil_8x8x8x8")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stencil-only", default=None, choices=sorted(STENCIL_LATTICES),
+                    help="only time the FP32 stencil matvec on this lattice (for profiling)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-restarts", type=int, default=4, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -344,6 +391,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.stencil_only:
+        print(json.dumps(stencil_apply_roofline(STENCIL_LATTICES[args.stencil_only])), flush=True)
         return
     if world > 1:
         import torch

@@ -82,7 +82,10 @@ typedef struct {
  *   (eq. (29)), 0 <= mwin.
  *   tol: convergence threshold on ||A x - lambda x|| with ||x|| = 1 (Algorithm 1, normal mode).
  *   which: JTRLAN_SMALLEST (smallest algebraic) or JTRLAN_LARGEST.
- *   precision: JTRLAN_FP64 (plain FP64 arithmetic throughout).  JTRLAN_MIXED is reserved.
+ *   precision: JTRLAN_FP64 -- plain FP64 arithmetic throughout.  JTRLAN_MIXED -- an FP32 phase
+ *     (matvec, Gram-Schmidt and basis rotation in FP32; alpha/beta accumulation, the Ritz solve and
+ *     the residual norms in FP64) run to max(tol, 1e-5 max|t|), then FP64 TRLAN-JSYM started from
+ *     the normalised sum of the FP32 Ritz vectors run to tol.  Results are FP64 in both modes.
  *   max_restarts: bound on outer iterations (N_conv); 0 selects 1000.
  *   gs_max_passes: bound on Gram-Schmidt passes per Lanczos step (Algorithm 2 has none);
  *     0 selects 3.
@@ -117,6 +120,8 @@ typedef struct {
   double solve_ms;         /* wall time of jtrlan_solve on the host clock */
   int64_t n_launches;      /* CUDA kernels launched by the solve */
   int n_ritz_fallbacks;    /* restarts whose fast Ritz solve failed a check (Jacobi used) */
+  int n_restarts_fp32;     /* JTRLAN_MIXED: outer iterations of the FP32 phase (in n_restarts) */
+  int64_t n_matvec_fp32;   /* JTRLAN_MIXED: products of the FP32 phase (included in n_matvec) */
 } jtrlan_stats;
 
 /* Per-kernel-class profile of the last solve (filled when jtrlan_params.profile was set; the
@@ -145,8 +150,9 @@ typedef struct jtrlan_ctx jtrlan_ctx;  /* opaque; owned by the library */
 jtrlan_status jtrlan_create(const jtrlan_operator* op, const jtrlan_params* params,
                             void* cuda_stream, jtrlan_ctx** out);
 
-/* y = A x in the canonical layout, both device pointers of n complex numbers in the context's
- * working precision (double2 for JTRLAN_FP64).  Enqueued on the context stream; no sync.
+/* y = A x in the canonical layout, both device pointers of n complex numbers: double2 for a
+ * JTRLAN_FP64 context, float2 (the FP32 operator of the first phase) for JTRLAN_MIXED.
+ * Enqueued on the context stream; no sync.
  * This is the Algorithm 2 product A v_j.  Errors: JTRLAN_EINVAL (null), JTRLAN_ECUDA. */
 jtrlan_status jtrlan_apply(jtrlan_ctx* ctx, const void* x, void* y);
 
@@ -158,8 +164,8 @@ jtrlan_status jtrlan_solve(jtrlan_ctx* ctx, jtrlan_stats* stats);
 /* Copies the converged pairs of the last successful solve, sorted by eigenvalue (ascending for
  * JTRLAN_SMALLEST, descending for JTRLAN_LARGEST).
  *   evals: host array of nev doubles (may be NULL).
- *   evecs: host or device array, column-major n x nev (or n x 2nev if with_partners), in the
- *     context's working precision (double2 for JTRLAN_FP64); may be NULL.  With partners,
+ *   evecs: host or device array, column-major n x nev (or n x 2nev if with_partners) of double2
+ *     (FP64 in both precision modes); may be NULL.  With partners,
  *     column nev + i holds y_i = J x_i^* (eq. (2)).
  *   res: host array of nev doubles, the true residuals ||A x_i - lambda_i x_i|| (may be NULL).
  * Synchronises the context stream.  Errors: JTRLAN_ESTATE if no solve has succeeded. */

@@ -44,7 +44,8 @@ class jtrlan_stats(ctypes.Structure):
     _fields_ = [("n_matvec", ctypes.c_int64), ("n_resid_matvec", ctypes.c_int64),
                 ("n_gs_passes", ctypes.c_int64), ("n_restarts", ctypes.c_int),
                 ("icnv", ctypes.c_int), ("solve_ms", ctypes.c_double), ("n_launches", ctypes.c_int64),
-                ("n_ritz_fallbacks", ctypes.c_int)]
+                ("n_ritz_fallbacks", ctypes.c_int), ("n_restarts_fp32", ctypes.c_int),
+                ("n_matvec_fp32", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -89,6 +89,18 @@ struct Profiler {
   }
 };
 
+// Operator copy and Krylov basis in one working precision.
+struct Phase {
+  OpDev op{};
+  void* V = nullptr;      // n x (m + 1)
+  void* Vtmp = nullptr;   // n x kk (rotation target)
+  void* y = nullptr;      // the vector being built
+  size_t cs = 0;          // bytes per complex number
+  double* alpha_part = nullptr;
+  double* resid_part = nullptr;
+  int mv_nblk = 0;
+};
+
 }  // namespace
 
 struct jtrlan_ctx {
@@ -98,12 +110,10 @@ struct jtrlan_ctx {
   OpDev op{};
   int64_t n = 0, h = 0;
   int m = 0, nev = 0, mwin = 0, kk = 0, max_restarts = 0, gs_passes = 0;
-  size_t csize = sizeof(double2);  // bytes per complex number of the working precision
+  bool mixed = false;              // JTRLAN_MIXED: an FP32 phase, then the FP64 phase
   std::vector<void*> owned;        // device allocations
   std::vector<void*> owned_host;   // pinned host allocations
-  void* V = nullptr;
-  void* Vtmp = nullptr;
-  void* y = nullptr;
+  Phase p64, p32;                  // per-precision operator copy and basis buffers
   double* T = nullptr;
   double* lam = nullptr;
   double* Z = nullptr;
@@ -114,8 +124,6 @@ struct jtrlan_ctx {
   double* part_nrm = nullptr;
   coef4* coef = nullptr;
   StepState* st = nullptr;
-  double* alpha_part = nullptr;
-  double* resid_part = nullptr;
   double* d_res = nullptr;
   double* d_candlam = nullptr;
   int* d_cand = nullptr;
@@ -132,8 +140,11 @@ struct jtrlan_ctx {
   int* h_perm = nullptr;
   int* h_order = nullptr;
   double* h_misc = nullptr;
-  int mv_nblk = 0, gs_nblk = 0, gs_rpb = 0;
+  int gs_nblk = 0, gs_rpb = 0;
   Profiler prof;
+  double work_base[3] = {};        // device work counters carried across solve phases
+  int fallback_base = 0;
+  int64_t gs_pass_base = 0;
   int64_t nl[K_NTAGS] = {};        // launches per kernel class in the last solve
   double work[K_NTAGS] = {};       // algorithmic work per kernel class in the last solve
   // results of the last solve
@@ -215,7 +226,7 @@ jtrlan_status validate(const jtrlan_operator* op, const jtrlan_params* p) {
   if (p->mwin < 0) return fail(JTRLAN_EINVAL, "need mwin >= 0");
   if (!(p->tol > 0.0)) return fail(JTRLAN_EINVAL, "need tol > 0");
   if (p->which != JTRLAN_SMALLEST && p->which != JTRLAN_LARGEST) return fail(JTRLAN_EINVAL, "unknown which");
-  if (p->precision != JTRLAN_FP64) return fail(JTRLAN_EINVAL, "only JTRLAN_FP64 is implemented");
+  if (p->precision != JTRLAN_FP64 && p->precision != JTRLAN_MIXED) return fail(JTRLAN_EINVAL, "unknown precision");
   if (p->gs_max_passes < 0 || p->gs_max_passes > 7) return fail(JTRLAN_EINVAL, "gs_max_passes must be 0..7");
   if (p->max_restarts < 0) return fail(JTRLAN_EINVAL, "max_restarts must be >= 0");
   return JTRLAN_OK;
@@ -237,13 +248,15 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   c->kk = std::min(prm->nev + prm->mwin, prm->m - 1);
   c->max_restarts = prm->max_restarts ? prm->max_restarts : 1000;
   c->gs_passes = prm->gs_max_passes ? prm->gs_max_passes : 3;
-  OpDev& o = c->op;
+  c->mixed = prm->precision == JTRLAN_MIXED;
+  OpDev& o = c->p64.op;
   o.kind = op->kind;
   o.n = c->n;
   o.h = c->h;
   o.m0 = op->m0;
   o.kappa = op->kappa;
   o.vol = 1;
+  o.fp32 = 0;
   for (int d = 0; d < 4; ++d) { o.dims[d] = op->dims[d]; if (op->kind == JTRLAN_STENCIL4D) o.vol *= op->dims[d]; }
   if (op->kind == JTRLAN_STENCIL4D) {
     void *u = nullptr, *w = nullptr;
@@ -258,12 +271,39 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   }
   const int m = c->m;
   const int mp = m + (m & 1);
-  c->mv_nblk = matvec_blocks(o);
   c->gs_nblk = gs_blocks(c->h, &c->gs_rpb);
-  const size_t cs = c->csize;
-  JT_TRY(c->dalloc(&c->V, (size_t)c->n * (m + 1) * cs));
-  JT_TRY(c->dalloc(&c->Vtmp, (size_t)c->n * std::max(c->kk, 1) * cs));
-  JT_TRY(c->dalloc(&c->y, (size_t)c->n * cs));
+  auto make_phase = [&](Phase& ph, size_t cs) -> jtrlan_status {
+    ph.cs = cs;
+    ph.mv_nblk = matvec_blocks(ph.op);
+    JT_TRY(c->dalloc(&ph.V, (size_t)c->n * (m + 1) * cs));
+    JT_TRY(c->dalloc(&ph.Vtmp, (size_t)c->n * std::max(c->kk, 1) * cs));
+    JT_TRY(c->dalloc(&ph.y, (size_t)c->n * cs));
+    JT_TRY(c->dalloc(&ph.alpha_part, (size_t)ph.mv_nblk * sizeof(double2)));
+    JT_TRY(c->dalloc(&ph.resid_part, (size_t)ph.mv_nblk * c->nev * sizeof(double)));
+    return JTRLAN_OK;
+  };
+  JT_TRY(make_phase(c->p64, sizeof(double2)));
+  if (c->mixed) {  // the FP32 operator: links re-laid out structure-of-arrays, or FP32 dense blocks
+    OpDev& q = c->p32.op;
+    q = o;
+    q.fp32 = 1;
+    if (op->kind == JTRLAN_STENCIL4D) {
+      float2 *u = nullptr, *w = nullptr;
+      JT_TRY(c->dalloc(&u, (size_t)36 * o.vol * sizeof(float2)));
+      JT_TRY(c->dalloc(&w, (size_t)36 * o.vol * sizeof(float2)));
+      JT_CUDA(launch_links_soa(o.U, u, o.vol, c->stream));
+      JT_CUDA(launch_links_soa(o.W, w, o.vol, c->stream));
+      q.U = u; q.W = w;
+    } else {
+      float2 *a = nullptr, *b = nullptr;
+      JT_TRY(c->dalloc(&a, (size_t)c->h * c->h * sizeof(float2)));
+      JT_TRY(c->dalloc(&b, (size_t)c->h * c->h * sizeof(float2)));
+      JT_CUDA(launch_c128_to_c64(o.a11, a, c->h * c->h, c->stream));
+      JT_CUDA(launch_c128_to_c64(o.a12, b, c->h * c->h, c->stream));
+      q.a11 = a; q.a12 = b;
+    }
+    JT_TRY(make_phase(c->p32, sizeof(float2)));
+  }
   JT_TRY(c->dalloc(&c->T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
   JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));
   JT_TRY(c->dalloc(&c->Z, (size_t)m * m * sizeof(double)));
@@ -273,8 +313,6 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   JT_TRY(c->dalloc(&c->part_nrm, (size_t)c->gs_nblk * sizeof(double)));
   JT_TRY(c->dalloc(&c->coef, (size_t)(m + 1) * sizeof(coef4)));
   JT_TRY(c->dalloc(&c->st, sizeof(StepState)));
-  JT_TRY(c->dalloc(&c->alpha_part, (size_t)c->mv_nblk * sizeof(double2)));
-  JT_TRY(c->dalloc(&c->resid_part, (size_t)c->mv_nblk * c->nev * sizeof(double)));
   JT_TRY(c->dalloc(&c->d_res, (size_t)c->nev * sizeof(double)));
   JT_TRY(c->dalloc(&c->d_candlam, (size_t)c->nev * sizeof(double)));
   JT_TRY(c->dalloc(&c->d_cand, (size_t)c->nev * sizeof(int)));
@@ -291,10 +329,10 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   JT_TRY(c->halloc(&c->h_order, (size_t)c->nev * sizeof(int)));
   JT_TRY(c->halloc(&c->h_misc, 16 * sizeof(double)));
   if (prm->check_jsym) {  // Lemma 1: (J v^*)^H A v = 0 for any v
-    JT_CUDA(launch_fill_random<double>(c->Vtmp, c->n, 0x5eed1234ull, c->stream));
-    JT_CUDA(launch_matvec<double>(o, (const double2*)c->Vtmp, (double2*)c->y, MV_PLAIN, nullptr, nullptr, nullptr, 0,
-                                  0, nullptr, c->stream));
-    JT_CUDA(launch_jsym_check<double>(c->Vtmp, c->y, c->h, c->d_misc, c->stream));
+    JT_CUDA(launch_fill_random<double>(c->p64.Vtmp, c->n, 0x5eed1234ull, c->stream));
+    JT_CUDA(launch_matvec<double>(o, (const double2*)c->p64.Vtmp, (double2*)c->p64.y, MV_PLAIN, nullptr, nullptr,
+                                  nullptr, 0, 0, nullptr, c->stream));
+    JT_CUDA(launch_jsym_check<double>(c->p64.Vtmp, c->p64.y, c->h, c->d_misc, c->stream));
     JT_CUDA(cudaMemcpyAsync(c->h_misc, c->d_misc, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     JT_CUDA(cudaStreamSynchronize(c->stream));
     const double wAv = std::hypot(c->h_misc[0], c->h_misc[1]);
@@ -311,17 +349,6 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
 
 inline void* col(void* base, int64_t n, int j, size_t cs) { return (char*)base + (size_t)j * n * cs; }
 
-jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
-  const auto t0 = std::chrono::steady_clock::now();
-  c->solved = false;
-  const int m = c->m, nev = c->nev, ldt = m + 1;
-  const int64_t n = c->n;
-  const size_t cs = c->csize;
-  cudaStream_t s = c->stream;
-  jtrlan_stats stt{};
-  c->prof.on = c->prm.profile != 0;
-  c->prof.used = 0;
-  for (int t = 0; t < K_NTAGS; ++t) { c->prof.ms[t] = 0; c->nl[t] = 0; c->work[t] = 0; }
 #define LAUNCH(tag, expr)                  \
   do {                                     \
     JT_CUDA(c->prof.begin((tag), s));      \
@@ -329,67 +356,73 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
     JT_CUDA(c->prof.end(s));               \
     c->nl[(tag)] += 1;                     \
   } while (0)
+
+// Algorithm 1 (TRLAN-JSYM) in working precision R from the start vector in ph.V[:, 0] (already
+// normalised), until nev pairs have true residual < tol (tol_rel_tmax > 0: the phase tolerance is
+// max(tol, tol_rel_tmax * max|t|), for the FP32 phase).  On success the converged Ritz vectors
+// are ph.V[:, 0..nev) with eigenvalues ev and residuals res (converged-first order).
+template <typename R>
+jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tmax, int max_restarts,
+                        jtrlan_stats& stt, std::vector<double>& ev, std::vector<double>& res, int* icnv_out) {
+  using C = cplx<R>;
+  const int m = c->m, nev = c->nev, ldt = m + 1, kk = c->kk;
+  const int64_t n = c->n;
+  const size_t cs = ph.cs;
+  cudaStream_t s = c->stream;
   JT_CUDA(cudaMemsetAsync(c->st, 0, sizeof(StepState), s));
   JT_CUDA(cudaMemsetAsync(c->T, 0, (size_t)ldt * ldt * sizeof(double), s));
-  if (c->prm.v1) {
-    if (c->opd.dtype != JTRLAN_C128) return fail(JTRLAN_EINVAL, "v1 must be complex128 for the FP64 solver");
-    JT_CUDA(cudaMemcpyAsync(c->V, c->prm.v1, (size_t)n * cs, cudaMemcpyDefault, s));
-    LAUNCH(K_OTHER, launch_normalize_col<double>(c->V, n, c->part_nrm, c->gs_nblk, s));
-    c->nl[K_OTHER] += 1;  // two kernels
-  } else {
-    LAUNCH(K_OTHER, launch_fill_ones<double>(c->V, n, s));  // v_1 = 1 / ||1||
-  }
   GSArgs a{};
-  a.V = c->V; a.n = n; a.h = c->h; a.y = c->y; a.part_dot = c->part_dot; a.part_nrm = c->part_nrm;
+  a.V = ph.V; a.n = n; a.h = c->h; a.y = ph.y; a.part_dot = c->part_dot; a.part_nrm = c->part_nrm;
   a.coef = c->coef; a.st = c->st; a.T = c->T; a.ldt = ldt; a.m = m; a.nblk = c->gs_nblk;
   a.rows_per_block = c->gs_rpb;
-  const double mv_units = c->op.kind == JTRLAN_STENCIL4D ? (double)c->op.vol : (double)c->h * (double)c->h;
-  std::vector<double> ev(nev), res(nev, INFINITY), res_est(nev), lamv(m), arrow(m);
+  const double mv_units = ph.op.kind == JTRLAN_STENCIL4D ? (double)ph.op.vol : (double)c->h * (double)c->h;
+  ev.assign(nev, 0.0);
+  res.assign(nev, INFINITY);
+  std::vector<double> res_est(nev), lamv(m), arrow(m);
   std::vector<char> conv(nev);
   std::vector<int> perm(m);
   int k = 0, icnv = 0;
-  for (int restart = 0; restart < c->max_restarts; ++restart) {
+  *icnv_out = 0;
+  for (int restart = 0; restart < max_restarts; ++restart) {
     // ---- Algorithm 2: m - k Lanczos steps, no host synchronisation inside
     for (int j = k; j < m; ++j) {
-      LAUNCH(K_MATVEC, launch_matvec<double>(c->op, (const double2*)col(c->V, n, j, cs), (double2*)c->y, MV_ALPHA,
-                                             c->alpha_part, nullptr, nullptr, 0, 0, nullptr, s));
+      LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)col(ph.V, n, j, cs), (C*)ph.y, MV_ALPHA, ph.alpha_part,
+                                        nullptr, nullptr, 0, 0, nullptr, s));
       a.j = j;
-      LAUNCH(K_GS_FIRST, launch_gs_first<double>(a, (const double2*)c->alpha_part, c->mv_nblk, s));
+      LAUNCH(K_GS_FIRST, launch_gs_first<R>(a, (const double2*)ph.alpha_part, ph.mv_nblk, s));
       LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
-      LAUNCH(K_GS_UPDATE, launch_gs_update<double>(a, s));
+      LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
       for (int pass = 2; pass <= c->gs_passes; ++pass) {
-        LAUNCH(K_GS_DOT, launch_gs_dot<double>(a, pass, s));
+        LAUNCH(K_GS_DOT, launch_gs_dot<R>(a, pass, s));
         LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
-        LAUNCH(K_GS_UPDATE, launch_gs_update<double>(a, s));
+        LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
       }
-      LAUNCH(K_GS_NORMALIZE, launch_gs_normalize<double>(a, s));
+      LAUNCH(K_GS_NORMALIZE, launch_gs_normalize<R>(a, s));
     }
     stt.n_matvec += m - k;
     c->work[K_MATVEC] += (double)(m - k) * mv_units;
     stt.n_restarts += 1;
-    // ---- Rayleigh-Ritz: T_m = Z Lambda Z^T, sorted; V_m Z into Vtmp
-    LAUNCH(K_RITZ, launch_ritz(c->T, ldt, m, k, c->kk, c->prm.which, c->lam, c->Z, c->ritz_flags, s));
+    // ---- Rayleigh-Ritz (FP64): T_m = Z Lambda Z^T, the kk wanted pairs; V_m Z into Vtmp
+    LAUNCH(K_RITZ, launch_ritz(c->T, ldt, m, k, kk, c->prm.which, c->lam, c->Z, c->ritz_flags, s));
     c->nl[K_RITZ] += 1;  // two kernels: bisection + inverse iteration, checks
     LAUNCH(K_RITZ_FALLBACK, launch_ritz_fallback(c->T, ldt, m, c->prm.which, c->lam, c->Z, c->work_ritz(),
                                                  c->ritz_flags, &c->st->n_ritz_fallbacks, s));
-    LAUNCH(K_ROTATE, launch_rotate<double>(c->V, n, m, c->Z, c->kk, c->Vtmp, s));
-    c->work[K_ROTATE] += 2.0 * (double)n * m * c->kk;
+    LAUNCH(K_ROTATE, launch_rotate<R>(ph.V, n, m, c->Z, kk, ph.Vtmp, s));
+    c->work[K_ROTATE] += 2.0 * (double)n * m * kk;
     LAUNCH(K_OTHER, launch_report(c->lam, c->Z, m, c->T, ldt, c->st, c->d_rep, s));
     JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * m + 8) * sizeof(double), cudaMemcpyDeviceToHost, s));
     JT_CUDA(cudaStreamSynchronize(s));
     JT_CUDA(c->prof.harvest());
-    stt.n_gs_passes = (int64_t)c->h_rep[2 * m + 2];
-    c->work[K_GS_FIRST] = c->h_rep[2 * m + 4];
-    c->work[K_GS_DOT] = c->h_rep[2 * m + 5];
-    c->work[K_GS_UPDATE] = c->h_rep[2 * m + 6];
-    stt.n_ritz_fallbacks = (int)c->h_rep[2 * m + 7];
-    if (c->h_rep[2 * m + 1] != 0.0) {
-      c->stats = stt;
-      if (stats_out) *stats_out = stt;
-      return fail(JTRLAN_EBREAKDOWN, "Lanczos breakdown: beta below 1e-14 max|T|");
-    }
+    stt.n_gs_passes += (int64_t)c->h_rep[2 * m + 2] - c->gs_pass_base;
+    c->gs_pass_base = (int64_t)c->h_rep[2 * m + 2];
+    c->work[K_GS_FIRST] = c->work_base[0] + c->h_rep[2 * m + 4];
+    c->work[K_GS_DOT] = c->work_base[1] + c->h_rep[2 * m + 5];
+    c->work[K_GS_UPDATE] = c->work_base[2] + c->h_rep[2 * m + 6];
+    stt.n_ritz_fallbacks = c->fallback_base + (int)c->h_rep[2 * m + 7];
+    if (c->h_rep[2 * m + 1] != 0.0) return fail(JTRLAN_EBREAKDOWN, "Lanczos breakdown: beta below 1e-14 max|T|");
+    const double tmax = c->h_rep[2 * m + 3];
+    const double tol_ph = std::max(tol, tol_rel_tmax * tmax);
     const double beta_m = c->h_rep[2 * m];
-    const int kk = c->kk;                     // Ritz pairs computed (nearest the wanted end)
     for (int i = 0; i < kk; ++i) {
       lamv[i] = c->h_rep[i];
       arrow[i] = beta_m * c->h_rep[m + i];   // t_{m+1,i} = t_{m+1,m} z_{m,i}
@@ -399,15 +432,15 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
       ev[i] = lamv[i];
       res_est[i] = std::fabs(arrow[i]);
       conv[i] = 0;                            // is_convd reset every outer iteration
-      if (res_est[i] < c->prm.tol) { c->h_cand[ncand] = i; c->h_candlam[ncand] = ev[i]; ++ncand; }
+      if (res_est[i] < tol_ph) { c->h_cand[ncand] = i; c->h_candlam[ncand] = ev[i]; ++ncand; }
     }
     if (ncand > 0) {  // true residuals ||A v_i - ev_i v_i|| of the candidates
       JT_CUDA(cudaMemcpyAsync(c->d_cand, c->h_cand, ncand * sizeof(int), cudaMemcpyHostToDevice, s));
       JT_CUDA(cudaMemcpyAsync(c->d_candlam, c->h_candlam, ncand * sizeof(double), cudaMemcpyHostToDevice, s));
-      LAUNCH(K_RESID, launch_matvec<double>(c->op, (const double2*)c->Vtmp, nullptr, MV_RESID, c->resid_part, c->d_cand,
-                                            c->d_candlam, ncand, n, nullptr, s));
+      LAUNCH(K_RESID, launch_matvec<R>(ph.op, (const C*)ph.Vtmp, nullptr, MV_RESID, ph.resid_part, c->d_cand,
+                                       c->d_candlam, ncand, n, nullptr, s));
       c->work[K_RESID] += (double)ncand * mv_units;
-      LAUNCH(K_OTHER, launch_reduce_norms(c->resid_part, c->mv_nblk, ncand, c->d_res, s));
+      LAUNCH(K_OTHER, launch_reduce_norms(ph.resid_part, ph.mv_nblk, ncand, c->d_res, s));
       JT_CUDA(cudaMemcpyAsync(c->h_res, c->d_res, ncand * sizeof(double), cudaMemcpyDeviceToHost, s));
       JT_CUDA(cudaStreamSynchronize(s));
       JT_CUDA(c->prof.harvest());
@@ -415,7 +448,7 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
       for (int q = 0; q < ncand; ++q) {
         const int i = c->h_cand[q];
         res[i] = c->h_res[q];
-        conv[i] = res[i] < c->prm.tol;
+        conv[i] = res[i] < tol_ph;
       }
     }
     // converged pairs to the top (stable), identity beyond nev
@@ -429,10 +462,11 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
     for (int i = 0; i < nev; ++i) { ev2[i] = ev[perm[i]]; res2[i] = res[perm[i]]; }
     ev = ev2; res = res2; lamv = lam2; arrow = arrow2;
     for (int i = 0; i < icnv; ++i) arrow[i] = 0.0;   // decouple the converged subspace
+    *icnv_out = icnv;
     if (icnv == nev) {
       for (int i = 0; i < m; ++i) c->h_perm[i] = perm[i];
       JT_CUDA(cudaMemcpyAsync(c->d_perm, c->h_perm, m * sizeof(int), cudaMemcpyHostToDevice, s));
-      LAUNCH(K_SHRINK, launch_shrink<double>(c->V, c->Vtmp, n, c->d_perm, nev, m, s));
+      LAUNCH(K_SHRINK, launch_shrink<R>(ph.V, ph.Vtmp, n, c->d_perm, nev, m, s));
       JT_CUDA(cudaStreamSynchronize(s));
       JT_CUDA(c->prof.harvest());
       break;
@@ -440,27 +474,93 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
     // ---- shrink to k + 1 (eq. (29)); T-bar = diag(lambda_1..k) with the arrow in row k+1
     k = std::min(icnv + c->mwin, m - 1);
     std::memset(c->h_T, 0, (size_t)ldt * ldt * sizeof(double));
-    double tmax = 0.0;
+    double tm = 0.0;
     for (int i = 0; i < k; ++i) {
       c->h_T[(size_t)i * ldt + i] = lamv[i];
       c->h_T[(size_t)k * ldt + i] = arrow[i];
       c->h_T[(size_t)i * ldt + k] = arrow[i];
-      tmax = std::max(tmax, std::max(std::fabs(lamv[i]), std::fabs(arrow[i])));
+      tm = std::max(tm, std::max(std::fabs(lamv[i]), std::fabs(arrow[i])));
     }
-    c->h_misc[0] = tmax;
+    c->h_misc[0] = tm;
     for (int i = 0; i < m; ++i) c->h_perm[i] = perm[i];
     JT_CUDA(cudaMemcpyAsync(c->T, c->h_T, (size_t)ldt * ldt * sizeof(double), cudaMemcpyHostToDevice, s));
     JT_CUDA(cudaMemcpyAsync(&c->st->tmax, c->h_misc, sizeof(double), cudaMemcpyHostToDevice, s));
     JT_CUDA(cudaMemcpyAsync(c->d_perm, c->h_perm, m * sizeof(int), cudaMemcpyHostToDevice, s));
-    LAUNCH(K_SHRINK, launch_shrink<double>(c->V, c->Vtmp, n, c->d_perm, k, m, s));  // and v_{k+1} = v_{m+1}
+    LAUNCH(K_SHRINK, launch_shrink<R>(ph.V, ph.Vtmp, n, c->d_perm, k, m, s));  // and v_{k+1} = v_{m+1}
   }
-#undef LAUNCH
+  // carry the device counters of this phase into the next one
+  c->work_base[0] = c->work[K_GS_FIRST];
+  c->work_base[1] = c->work[K_GS_DOT];
+  c->work_base[2] = c->work[K_GS_UPDATE];
+  c->fallback_base = stt.n_ritz_fallbacks;
+  c->gs_pass_base = 0;
+  if (icnv != nev) return fail(JTRLAN_ENOCONV, "max_restarts reached before nev pairs converged");
+  return JTRLAN_OK;
+}
+
+jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
+  const auto t0 = std::chrono::steady_clock::now();
+  c->solved = false;
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  jtrlan_stats stt{};
+  c->prof.on = c->prm.profile != 0;
+  c->prof.used = 0;
+  for (int t = 0; t < K_NTAGS; ++t) { c->prof.ms[t] = 0; c->nl[t] = 0; c->work[t] = 0; }
+  for (int t = 0; t < 3; ++t) c->work_base[t] = 0;
+  c->fallback_base = 0;
+  c->gs_pass_base = 0;
+  std::vector<double> ev, res;
+  int icnv = 0;
+  jtrlan_status st = JTRLAN_OK;
+  if (c->prm.v1 && c->opd.dtype != JTRLAN_C128) return fail(JTRLAN_EINVAL, "v1 must be complex128");
+  if (c->mixed) {
+    // FP32 phase: matvec, Gram-Schmidt and rotation in FP32, alpha/beta and Ritz in FP64, to the
+    // tolerance max(tol, 1e-5 max|t|) that FP32 vectors can certify.
+    Phase& ph = c->p32;
+    if (c->prm.v1) {
+      JT_CUDA(cudaMemcpyAsync(c->p64.y, c->prm.v1, (size_t)n * sizeof(double2), cudaMemcpyDefault, s));
+      LAUNCH(K_OTHER, launch_c128_to_c64(c->p64.y, ph.V, n, s));
+    } else {
+      LAUNCH(K_OTHER, launch_fill_ones<float>(ph.V, n, s));
+    }
+    LAUNCH(K_OTHER, launch_normalize_col<float>(ph.V, n, c->part_nrm, c->gs_nblk, s));
+    c->nl[K_OTHER] += 1;
+    jtrlan_stats s32{};
+    st = run_phase<float>(c, ph, c->prm.tol, 1e-5, c->max_restarts, s32, ev, res, &icnv);
+    if (st != JTRLAN_OK && st != JTRLAN_ENOCONV) return st;
+    stt.n_matvec_fp32 = s32.n_matvec;
+    stt.n_matvec += s32.n_matvec;
+    stt.n_resid_matvec += s32.n_resid_matvec;
+    stt.n_gs_passes += s32.n_gs_passes;
+    stt.n_restarts_fp32 = s32.n_restarts;
+    stt.n_restarts += s32.n_restarts;
+    // FP64 phase starts from the normalised sum of the FP32 Ritz vectors (promoted)
+    LAUNCH(K_OTHER, launch_sum_columns(ph.V, n, std::max(icnv, 1), c->p64.V, s));
+    LAUNCH(K_OTHER, launch_normalize_col<double>(c->p64.V, n, c->part_nrm, c->gs_nblk, s));
+    c->nl[K_OTHER] += 1;
+  } else {
+    if (c->prm.v1) {
+      JT_CUDA(cudaMemcpyAsync(c->p64.V, c->prm.v1, (size_t)n * sizeof(double2), cudaMemcpyDefault, s));
+      LAUNCH(K_OTHER, launch_normalize_col<double>(c->p64.V, n, c->part_nrm, c->gs_nblk, s));
+      c->nl[K_OTHER] += 1;  // two kernels
+    } else {
+      LAUNCH(K_OTHER, launch_fill_ones<double>(c->p64.V, n, s));  // v_1 = 1 / ||1||
+    }
+  }
+  jtrlan_stats s64{};
+  st = run_phase<double>(c, c->p64, c->prm.tol, 0.0, c->max_restarts, s64, ev, res, &icnv);
+  stt.n_matvec += s64.n_matvec;
+  stt.n_resid_matvec += s64.n_resid_matvec;
+  stt.n_gs_passes += s64.n_gs_passes;
+  stt.n_restarts += s64.n_restarts;
+  stt.n_ritz_fallbacks = s64.n_ritz_fallbacks;
   stt.icnv = icnv;
   for (int t = 0; t < K_NTAGS; ++t) stt.n_launches += c->nl[t];
   stt.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   c->stats = stt;
   if (stats_out) *stats_out = stt;
-  if (icnv != nev) return fail(JTRLAN_ENOCONV, "max_restarts reached before nev pairs converged");
+  if (st != JTRLAN_OK) return st;
   c->ev = ev;
   c->res = res;
   c->solved = true;
@@ -488,8 +588,12 @@ jtrlan_status jtrlan_create(const jtrlan_operator* op, const jtrlan_params* para
 
 jtrlan_status jtrlan_apply(jtrlan_ctx* c, const void* x, void* y) {
   if (!c || !x || !y) return fail(JTRLAN_EINVAL, "null argument");
-  JT_CUDA(launch_matvec<double>(c->op, (const double2*)x, (double2*)y, MV_PLAIN, nullptr, nullptr, nullptr, 0, 0,
-                                nullptr, c->stream));
+  if (c->mixed)
+    JT_CUDA(launch_matvec<float>(c->p32.op, (const float2*)x, (float2*)y, MV_PLAIN, nullptr, nullptr, nullptr, 0, 0,
+                                 nullptr, c->stream));
+  else
+    JT_CUDA(launch_matvec<double>(c->p64.op, (const double2*)x, (double2*)y, MV_PLAIN, nullptr, nullptr, nullptr, 0,
+                                  0, nullptr, c->stream));
   return JTRLAN_OK;
 }
 
@@ -516,17 +620,17 @@ jtrlan_status jtrlan_pairs(jtrlan_ctx* c, int with_partners, double* evals, void
     for (int i = 0; i < nev; ++i) c->h_order[i] = order[i];
     JT_CUDA(cudaMemcpyAsync(c->d_order, c->h_order, nev * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     const int ncols = with_partners ? 2 * nev : nev;
-    const size_t bytes = (size_t)c->n * ncols * c->csize;
+    const size_t bytes = (size_t)c->n * ncols * sizeof(double2);
     cudaPointerAttributes attr{};
     const bool dev = cudaPointerGetAttributes(&attr, evecs) == cudaSuccess &&
                      (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
     cudaGetLastError();
     if (dev) {
-      JT_CUDA(launch_gather_pairs<double>(c->V, c->n, c->d_order, nev, with_partners, evecs, c->stream));
+      JT_CUDA(launch_gather_pairs<double>(c->p64.V, c->n, c->d_order, nev, with_partners, evecs, c->stream));
     } else {
       void* tmp = nullptr;
       JT_CUDA(cudaMallocAsync(&tmp, bytes, c->stream));
-      JT_CUDA(launch_gather_pairs<double>(c->V, c->n, c->d_order, nev, with_partners, tmp, c->stream));
+      JT_CUDA(launch_gather_pairs<double>(c->p64.V, c->n, c->d_order, nev, with_partners, tmp, c->stream));
       JT_CUDA(cudaMemcpyAsync(evecs, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
       JT_CUDA(cudaFreeAsync(tmp, c->stream));
     }

@@ -35,9 +35,17 @@ template <typename C> __device__ __forceinline__ C cfmac(C a, C b, C acc) {
 template <typename C> __device__ __forceinline__ double cabs2(C a) {
   return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
 }
+// |a|^2 in the working precision (FP32 partial sums stay on the FP32 pipe)
+template <typename C> __device__ __forceinline__ auto cabs2w(C a) -> decltype(a.x) { return a.x * a.x + a.y * a.y; }
 
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;

@@ -46,8 +46,9 @@ __device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1
       C nv2 = v2; nv2.x = -nv2.x; nv2.y = -nv2.y;
       cw = cfma(nv2, y1, cw);
     }
-    const double s0 = warp_sum((double)cv.x), s1 = warp_sum((double)cv.y);
-    const double s2 = warp_sum((double)cw.x), s3 = warp_sum((double)cw.y);
+    // lane sums in the working precision, block partials in FP64
+    const double s0 = (double)warp_sum(cv.x), s1 = (double)warp_sum(cv.y);
+    const double s2 = (double)warp_sum(cw.x), s3 = (double)warp_sum(cw.y);
     if (lane == 0) {
       coef4 c; c.vr = s0; c.vi = s1; c.wr = s2; c.wi = s3;
       out[(int64_t)i * a.nblk + blockIdx.x] = c;
@@ -86,7 +87,7 @@ gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_pa
   const int64_t h = a.h;
   const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
   const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
-  double nrm = 0.0;
+  R nrm_r = 0;
   for (int64_t p = p0 + threadIdx.x; p < p1; p += kGsThreads) {
     C y1 = y[p], y2 = y[h + p];
     const C v1 = vj[p], v2 = vj[h + p];
@@ -94,9 +95,9 @@ gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_pa
     y2.x -= alpha * v2.x; y2.y -= alpha * v2.y;
     y[p] = y1;
     y[h + p] = y2;
-    nrm += cabs2(y1) + cabs2(y2);
+    nrm_r += cabs2w(y1) + cabs2w(y2);
   }
-  nrm = block_sum(nrm, sh);  // its barriers also publish the y writes to the whole block
+  const double nrm = block_sum((double)nrm_r, sh);  // its barriers also publish the y writes to the whole block
   if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
   dot_body<R>(a, p0, p1);
 }
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(kGsThreads) gs_update_kernel(GSArgs a) {
   const int64_t n = a.n, h = a.h;
   const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
   const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
-  double nrm = 0.0;
+  R nrm_r = 0;
   for (int64_t pb = p0; pb < p1; pb += 32) {
     const int64_t p = pb + lane;
     const bool ok = p < p1;
@@ -210,11 +211,11 @@ __global__ void __launch_bounds__(kGsThreads) gs_update_kernel(GSArgs a) {
       const C y1 = csub(y[p], s1), y2 = csub(y[h + p], s2);
       y[p] = y1;
       y[h + p] = y2;
-      nrm += cabs2(y1) + cabs2(y2);
+      nrm_r += cabs2w(y1) + cabs2w(y2);
     }
     __syncthreads();
   }
-  nrm = block_sum(nrm, sh);
+  const double nrm = block_sum((double)nrm_r, sh);
   if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
 }
 
@@ -263,6 +264,36 @@ template <typename R>
 __global__ void fill_random_kernel(cplx<R>* v, int64_t n, uint64_t seed) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = mk<R>((R)u01_sym(seed + 2 * (uint64_t)i), (R)u01_sym(seed + 2 * (uint64_t)i + 1));
+}
+
+// v64 = sum of the first ncol columns of an FP32 basis (ld n), promoted to FP64.
+__global__ void sum_columns_kernel(const float2* X, int64_t n, int ncol, double2* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < ncol; ++c) {
+      const float2 v = X[(int64_t)c * n + i];
+      re += v.x;
+      im += v.y;
+    }
+    out[i] = make_double2(re, im);
+  }
+}
+
+__global__ void c128_to_c64_kernel(const double2* in, float2* out, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// FP64 links [4][V][9] -> FP32 structure-of-arrays [4][9][V].
+__global__ void links_soa_kernel(const double2* in, float2* out, int64_t vol) {
+  const int64_t total = 36 * vol;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = q % vol;
+    const int64_t me = q / vol;            // mu * 9 + e
+    const int64_t mu = me / 9, e = me % 9;
+    const double2 v = in[(mu * vol + s) * 9 + e];
+    out[q] = make_float2((float)v.x, (float)v.y);
+  }
 }
 
 template <typename R>
@@ -367,7 +398,28 @@ cudaError_t launch_jsym_check(const void* v, const void* y, int64_t h, double* o
   return cudaGetLastError();
 }
 
+cudaError_t launch_sum_columns(const void* X32, int64_t n, int ncol, void* out64, cudaStream_t s) {
+  sum_columns_kernel<<<1024, 256, 0, s>>>((const float2*)X32, n, ncol, (double2*)out64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c128_to_c64(const void* in, void* out, int64_t count, cudaStream_t s) {
+  c128_to_c64_kernel<<<1024, 256, 0, s>>>((const double2*)in, (float2*)out, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_links_soa(const void* in, void* out, int64_t vol, cudaStream_t s) {
+  links_soa_kernel<<<1024, 256, 0, s>>>((const double2*)in, (float2*)out, vol);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_gs_first<double>(const GSArgs&, const double2*, int, cudaStream_t);
+template cudaError_t launch_gs_first<float>(const GSArgs&, const double2*, int, cudaStream_t);
+template cudaError_t launch_gs_update<float>(const GSArgs&, cudaStream_t);
+template cudaError_t launch_gs_dot<float>(const GSArgs&, int, cudaStream_t);
+template cudaError_t launch_gs_normalize<float>(const GSArgs&, cudaStream_t);
+template cudaError_t launch_fill_ones<float>(void*, int64_t, cudaStream_t);
+template cudaError_t launch_normalize_col<float>(void*, int64_t, double*, int, cudaStream_t);
 template cudaError_t launch_gs_update<double>(const GSArgs&, cudaStream_t);
 template cudaError_t launch_gs_dot<double>(const GSArgs&, int, cudaStream_t);
 template cudaError_t launch_gs_normalize<double>(const GSArgs&, cudaStream_t);

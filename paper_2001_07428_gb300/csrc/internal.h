@@ -19,8 +19,9 @@ struct OpDev {
   double m0, kappa;
   const void* a11;     // dense blocks (h x h row-major), working precision
   const void* a12;
-  const void* U;       // stencil links [4][V][9], working precision
+  const void* U;       // stencil links: FP64 [4][V][9]; FP32 structure-of-arrays [4][9][V]
   const void* W;
+  int fp32;            // 1: FP32 operator (float2 links / blocks), 0: FP64
 };
 
 // Modes of the matvec kernels.
@@ -113,6 +114,12 @@ cudaError_t launch_fill_random(void* v, int64_t n, uint64_t seed, cudaStream_t s
 // Gathers lam[0..m), Z[m-1, 0..m), T[m][m-1], st->status into rep[2m + 2].
 cudaError_t launch_report(const double* lam, const double* Z, int m, const double* T, int ldt,
                           const StepState* st, double* rep, cudaStream_t s);
+
+// Mixed precision helpers: out64 = sum of the first ncol FP32 columns (promoted); FP64 -> FP32
+// copies; FP64 links [4][V][9] to FP32 structure-of-arrays [4][9][V].
+cudaError_t launch_sum_columns(const void* X32, int64_t n, int ncol, void* out64, cudaStream_t s);
+cudaError_t launch_c128_to_c64(const void* in, void* out, int64_t count, cudaStream_t s);
+cudaError_t launch_links_soa(const void* in, void* out, int64_t vol, cudaStream_t s);
 
 // Sets the thread-local text returned by jtrlan_last_error().
 void set_last_error(const char* msg);

@@ -114,6 +114,110 @@ stencil_kernel(OpDev op, const cplx<R>* __restrict__ X, cplx<R>* __restrict__ Y,
   }
 }
 
+// FP32 (mixed-precision) stencil, HBM-bound: one thread per (site, colour a) computes y1[a] and
+// y2[a].  The three colour threads of a site split its 144 incident link words (row a of U(s),
+// W(s) and column a of U(s-mu), W(s-mu) for each direction) with no overlap, which keeps the live
+// state small.  A block holds all three colours of 128 consecutive sites (warps are colour-uniform):
+// element (r, c) of a link is read forward by colour r of its site and backward by colour c of the
+// next site along mu, at most ~54 blocks later, so the second read hits L2 and DRAM sees each link
+// once.  Links are stored structure-of-arrays, L[(mu*9 + e)*V + s], so every link load of a warp
+// is one contiguous 256-byte segment.  Index arithmetic is 32-bit.
+// 64 sites (192 threads) per block and at least 5 resident blocks per SM: measured best on GB300
+// (4.8 TB/s at 24^3 x 48), with each direction's 24 loads issued before its arithmetic.
+constexpr int kSitesPerBlock = 64;
+constexpr int kSiteThreads = 3 * kSitesPerBlock;
+constexpr int kSiteMinBlocks = 5;
+
+template <int MODE>
+__global__ void __launch_bounds__(kSiteThreads, kSiteMinBlocks)
+stencil_site_kernel(OpDev op, const float2* __restrict__ X, float2* __restrict__ Y, double* __restrict__ part,
+                    const int* __restrict__ cand, const double* __restrict__ lam, int64_t ldx) {
+  __shared__ double sh[32];
+  const int vol = (int)op.vol;
+  const int64_t h = op.h;
+  const int s = blockIdx.x * kSitesPerBlock + (threadIdx.x % kSitesPerBlock);
+  const int a = threadIdx.x / kSitesPerBlock;
+  const int col = blockIdx.y;
+  const float2* x = X + (MODE == MV_RESID ? (int64_t)cand[col] * ldx : 0);
+  double c0 = 0.0, c1 = 0.0;
+  if (s < vol) {
+    const float2* U = (const float2*)op.U;
+    const float2* W = (const float2*)op.W;
+    const float2* x1 = x;
+    const float2* x2 = x + h;
+    float2 y1 = make_float2(0.f, 0.f), y2 = y1, w1 = y1, w2 = y1;
+    int coord[4];
+    {
+      int r = s;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) { coord[d] = r % op.dims[d]; r /= op.dims[d]; }
+      coord[3] = r;
+    }
+    int stride = 1;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int L = op.dims[mu];
+      const int c = coord[mu];
+      const int sp = (c == L - 1) ? s - (L - 1) * stride : s + stride;
+      const int sm = (c == 0) ? s + (L - 1) * stride : s - stride;
+      stride *= L;
+      const float2* Um = U + (int64_t)mu * 9 * vol;
+      const float2* Wm = W + (int64_t)mu * 9 * vol;
+      float2 P1[3], P2[3], M1[3], M2[3], UF[3], UB[3], WF[3], WB[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        UF[b] = Um[(a * 3 + b) * vol + s];
+        UB[b] = Um[(b * 3 + a) * vol + sm];
+        WF[b] = Wm[(a * 3 + b) * vol + s];
+        WB[b] = Wm[(b * 3 + a) * vol + sm];
+      }
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        P1[b] = x1[3 * sp + b]; P2[b] = x2[3 * sp + b];
+        M1[b] = x1[3 * sm + b]; M2[b] = x2[3 * sm + b];
+      }
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float2 p1 = P1[b], p2 = P2[b], m1 = M1[b], m2 = M2[b];
+        // uf = U(s)_{ab}, ub = U(s-mu)_{ba}, wf = W(s)_{ab}, wb = W(s-mu)_{ba}
+        const float2 uf = UF[b], ub = UB[b], wf = WF[b], wb = WB[b];
+        y1 = cfma(uf, p1, y1);                          // U(s) x1(s+mu)
+        y1 = cfmac(ub, m1, y1);                         // U(s-mu)^H x1(s-mu)
+        y2 = cfmac(uf, p2, y2);                         // U(s)^* x2(s+mu)
+        y2 = cfma(ub, m2, y2);                          // U(s-mu)^T x2(s-mu)
+        w1 = cfma(wf, p2, w1);                          // W(s) x2(s+mu)
+        w1 = cfma(make_float2(-wb.x, -wb.y), m2, w1);   // -W(s-mu)^T x2(s-mu)
+        w2 = cfmac(make_float2(-wf.x, -wf.y), p1, w2);  // -W(s)^* x1(s+mu)
+        w2 = cfmac(wb, m1, w2);                         // +W(s-mu)^H x1(s-mu)
+      }
+    }
+    const float kap = (float)op.kappa, m0 = (float)op.m0;
+    const int64_t e1 = 3 * (int64_t)s + a;
+    const float2 xa = x1[e1], xb = x2[e1];
+    const float2 o1 = make_float2(y1.x + kap * w1.x + m0 * xa.x, y1.y + kap * w1.y + m0 * xa.y);
+    const float2 o2 = make_float2(y2.x + kap * w2.x + m0 * xb.x, y2.y + kap * w2.y + m0 * xb.y);
+    if (MODE != MV_RESID) { Y[e1] = o1; Y[h + e1] = o2; }
+    if (MODE == MV_ALPHA) {
+      c0 = (double)(xa.x * o1.x + xa.y * o1.y + xb.x * o2.x + xb.y * o2.y);
+      c1 = (double)(xa.x * o1.y - xa.y * o1.x + xb.x * o2.y - xb.y * o2.x);
+    } else if (MODE == MV_RESID) {
+      const float l = (float)lam[col];
+      const float r0 = o1.x - l * xa.x, r1 = o1.y - l * xa.y, r2 = o2.x - l * xb.x, r3 = o2.y - l * xb.y;
+      c0 = (double)(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+    }
+  }
+  const int64_t blk = blockIdx.x;     // block index within one product
+  const int64_t nblk = gridDim.x;
+  if (MODE == MV_ALPHA) {
+    c0 = block_sum(c0, sh);
+    c1 = block_sum(c1, sh);
+    if (threadIdx.x == 0) ((double2*)part)[blk] = make_double2(c0, c1);
+  } else if (MODE == MV_RESID) {
+    c0 = block_sum(c0, sh);
+    if (threadIdx.x == 0) part[(int64_t)col * nblk + blk] = c0;
+  }
+}
+
 // Dense: one warp per row r of the blocks; y1[r] and y2[r] from one read of row r of A11, A12.
 constexpr int kDenseRowsPerBlock = kMvThreads / 32;
 
@@ -174,17 +278,24 @@ template <typename R, int MODE>
 cudaError_t launch_mode(const OpDev& op, const cplx<R>* x, cplx<R>* y, double* part, const int* cand,
                         const double* lam, int ncand, int64_t ldx, int nblk, cudaStream_t s) {
   dim3 grid(nblk, MODE == MV_RESID ? ncand : 1);
-  if (op.kind == JTRLAN_STENCIL4D)
-    stencil_kernel<R, MODE><<<grid, kMvThreads, 0, s>>>(op, x, y, part, cand, lam, ldx);
-  else
+  if (op.kind == JTRLAN_STENCIL4D) {
+    if constexpr (sizeof(R) == sizeof(float))
+      stencil_site_kernel<MODE><<<grid, kSiteThreads, 0, s>>>(op, x, y, part, cand, lam, ldx);
+    else
+      stencil_kernel<R, MODE><<<grid, kMvThreads, 0, s>>>(op, x, y, part, cand, lam, ldx);
+  } else {
     dense_kernel<R, MODE><<<grid, kMvThreads, 0, s>>>(op, x, y, part, cand, lam, ldx);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
 int matvec_blocks(const OpDev& op) {
-  if (op.kind == JTRLAN_STENCIL4D) return (int)((24 * op.vol + kMvThreads - 1) / kMvThreads);
+  if (op.kind == JTRLAN_STENCIL4D) {
+    if (op.fp32) return (int)((op.vol + kSitesPerBlock - 1) / kSitesPerBlock);
+    return (int)((24 * op.vol + kMvThreads - 1) / kMvThreads);
+  }
   return (int)((op.h + kDenseRowsPerBlock - 1) / kDenseRowsPerBlock);
 }
 
@@ -204,5 +315,7 @@ cudaError_t launch_matvec(const OpDev& op, const cplx<R>* x, cplx<R>* y, MvMode 
 
 template cudaError_t launch_matvec<double>(const OpDev&, const double2*, double2*, MvMode, double*, const int*,
                                            const double*, int, int64_t, int*, cudaStream_t);
+template cudaError_t launch_matvec<float>(const OpDev&, const float2*, float2*, MvMode, double*, const int*,
+                                          const double*, int, int64_t, int*, cudaStream_t);
 
 }  // namespace jtr

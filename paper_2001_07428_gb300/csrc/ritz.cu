@@ -446,6 +446,55 @@ rotate_kernel(const R* __restrict__ V, int64_t rows, int m, const double* __rest
   }
 }
 
+// FP32 rotation for the mixed-precision phase: Z rounded to FP32, FP32 accumulation.
+__global__ void __launch_bounds__(256)
+rotate32_kernel(const float* __restrict__ V, int64_t rows, int m, const double* __restrict__ Z, int kk,
+                float* __restrict__ out) {
+  constexpr int BM = 128, BN = 32, BK = 16;
+  __shared__ float As[BK][BM];
+  __shared__ float Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int col0 = blockIdx.y * BN;
+  const int tr = tid % 32, tc = tid / 32;  // rows tr + 32 i (i < 4), cols tc + 8 j (j < 4)
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < m; k0 += BK) {
+    for (int e = tid; e < BK * BM; e += 256) {
+      const int kx = e / BM, r = e % BM;
+      const int64_t gr = row0 + r;
+      As[kx][r] = (gr < rows && k0 + kx < m) ? V[(int64_t)(k0 + kx) * rows + gr] : 0.f;
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      const int kx = e / BN, c = e % BN;
+      Bs[kx][c] = (k0 + kx < m && col0 + c < kk) ? (float)Z[(int64_t)(col0 + c) * m + k0 + kx] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int x = 0; x < BK; ++x) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[x][tr + 32 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[x][tc + 8 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = row0 + tr + 32 * i;
+    if (gr >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tc + 8 * j;
+      if (gc < kk) out[(int64_t)gc * rows + gr] = acc[i][j];
+    }
+  }
+}
+
 template <typename R>
 __global__ void shrink_kernel(cplx<R>* V, const cplx<R>* Vsrc, int64_t n, const int* perm, int k, int m) {
   const int c = blockIdx.y;
@@ -493,7 +542,7 @@ __global__ void report_kernel(const double* lam, const double* Z, int m, const d
     rep[2 * m] = T[(int64_t)m * ldt + m - 1];    // t_{m+1,m} = beta_m
     rep[2 * m + 1] = (double)st->status;
     rep[2 * m + 2] = (double)st->n_passes;
-    rep[2 * m + 3] = st->alpha_im;
+    rep[2 * m + 3] = st->tmax;
     rep[2 * m + 4] = st->units_first;
     rep[2 * m + 5] = st->units_dot;
     rep[2 * m + 6] = st->units_update;
@@ -553,6 +602,11 @@ cudaError_t launch_ritz_jacobi(const double* T, int ldt, int m, int which, doubl
 template <typename R>
 cudaError_t launch_rotate(const void* V, int64_t n, int m, const double* Z, int kk, void* Vout, cudaStream_t s) {
   const int64_t rows = 2 * n;
+  if constexpr (sizeof(R) == sizeof(float)) {
+    dim3 grid((unsigned)((rows + 127) / 128), (unsigned)((kk + 31) / 32));
+    rotate32_kernel<<<grid, 256, 0, s>>>((const float*)V, rows, m, Z, kk, (float*)Vout);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((kk + 31) / 32));
   rotate_kernel<R><<<grid, 256, 0, s>>>((const R*)V, rows, m, Z, kk, (R*)Vout);
   return cudaGetLastError();
@@ -586,6 +640,8 @@ cudaError_t launch_report(const double* lam, const double* Z, int m, const doubl
 }
 
 template cudaError_t launch_rotate<double>(const void*, int64_t, int, const double*, int, void*, cudaStream_t);
+template cudaError_t launch_rotate<float>(const void*, int64_t, int, const double*, int, void*, cudaStream_t);
+template cudaError_t launch_shrink<float>(void*, const void*, int64_t, const int*, int, int, cudaStream_t);
 template cudaError_t launch_shrink<double>(void*, const void*, int64_t, const int*, int, int, cudaStream_t);
 template cudaError_t launch_gather_pairs<double>(const void*, int64_t, const int*, int, int, void*, cudaStream_t);
 

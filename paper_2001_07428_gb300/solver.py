@@ -25,7 +25,7 @@ class JTRLan:
 
     def __init__(self, kind, *, nev, m, mwin, tol, which="smallest", dims=None, m0=None, kappa=None,
                  U=None, W=None, A11=None, A12=None, v1=None, max_restarts=0, gs_max_passes=0,
-                 check_jsym=False, profile=False, device="cuda"):
+                 check_jsym=False, profile=False, precision="fp64", device="cuda"):
         B.load()
         self.device = torch.device(device)
         self.stream = torch.cuda.current_stream(self.device)
@@ -49,14 +49,19 @@ class JTRLan:
             v1p = v1d.data_ptr()
         w = B.JTRLAN_LARGEST if which == "largest" else B.JTRLAN_SMALLEST
         self._keep_v1 = keep[-1] if v1 is not None else None
-        prm = B.params(nev, m, mwin, tol, which=w, max_restarts=max_restarts,
+        self.mixed = precision == "mixed"
+        prec = B.JTRLAN_MIXED if self.mixed else B.JTRLAN_FP64
+        prm = B.params(nev, m, mwin, tol, which=w, precision=prec, max_restarts=max_restarts,
                        gs_max_passes=gs_max_passes, v1_ptr=v1p, check_jsym=int(check_jsym),
                        profile=int(profile))
         self.ctx = B.jtrlan_create(op, prm, self.stream.cuda_stream)
         # jtrlan_create copied the operator; v1 is read at solve time, so it is kept alive.
 
     def apply(self, x: torch.Tensor) -> torch.Tensor:
+        """y = A x: complex128 for an FP64 context, complex64 (the FP32 operator) for a mixed one."""
         x = _dev(x, self.device)
+        if self.mixed:
+            x = x.to(torch.complex64)
         y = torch.empty_like(x)
         B.jtrlan_apply(self.ctx, x.data_ptr(), y.data_ptr())
         return y

@@ -51,8 +51,9 @@ int main(void) {
          offsetof(jtrlan_operator, m0), offsetof(jtrlan_operator, a11), offsetof(jtrlan_operator, W));
   printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_params), offsetof(jtrlan_params, tol),
          offsetof(jtrlan_params, v1), offsetof(jtrlan_params, check_jsym), offsetof(jtrlan_params, profile));
-  printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_stats), offsetof(jtrlan_stats, n_restarts),
-         offsetof(jtrlan_stats, solve_ms), offsetof(jtrlan_stats, n_launches), offsetof(jtrlan_stats, n_ritz_fallbacks));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_stats), offsetof(jtrlan_stats, n_restarts),
+         offsetof(jtrlan_stats, solve_ms), offsetof(jtrlan_stats, n_launches), offsetof(jtrlan_stats, n_ritz_fallbacks),
+         offsetof(jtrlan_stats, n_matvec_fp32));
   printf("%zu %zu %zu %zu\n", sizeof(jtrlan_profile), offsetof(jtrlan_profile, ms),
          offsetof(jtrlan_profile, launches), offsetof(jtrlan_profile, work));
   return 0;
@@ -64,7 +65,7 @@ int main(void) {
     assert got[0] == [ctypes.sizeof(O), O.n.offset, O.m0.offset, O.a11.offset, O.W.offset]
     assert got[1] == [ctypes.sizeof(P), P.tol.offset, P.v1.offset, P.check_jsym.offset, P.profile.offset]
     assert got[2] == [ctypes.sizeof(S), S.n_restarts.offset, S.solve_ms.offset, S.n_launches.offset,
-                      S.n_ritz_fallbacks.offset]
+                      S.n_ritz_fallbacks.offset, S.n_matvec_fp32.offset]
     assert got[3] == [ctypes.sizeof(F), F.ms.offset, F.launches.offset, F.work.offset]
 
 
@@ -77,7 +78,7 @@ DUMMY = 0x1000  # never dereferenced: validation fails before any copy
 
 
 @pytest.mark.parametrize("case", ["odd_n", "stencil_n", "nev_ge_m", "m_ge_half", "neg_mwin", "tol",
-                                  "which", "null_links", "kind", "precision"])
+                                  "which", "null_links", "kind", "precision", "big_m"])
 def test_invalid_arguments_rejected_without_gpu(lib, case):
     op = B.stencil_operator((4, 4, 4, 4), 8.5, 0.3, DUMMY, DUMMY)
     prm = B.params(6, 24, 12, 1e-10)
@@ -101,6 +102,9 @@ def test_invalid_arguments_rejected_without_gpu(lib, case):
         op.kind = 9
     elif case == "precision":
         prm.precision = 5
+    elif case == "big_m":
+        op = B.dense_operator(4000, DUMMY, DUMMY)
+        prm.m = 1024
     with pytest.raises(B.JTRLanError) as ei:
         B.jtrlan_create(op, prm, 0)
     assert ei.value.status == B.JTRLAN_EINVAL

@@ -200,3 +200,48 @@ def test_solve_twice_is_reproducible():
     assert st1["n_matvec"] == st2["n_matvec"]
     assert np.array_equal(ev1, ev2)
     assert torch.equal(X1, X2)
+
+
+# ----------------------------------------------------------------------------- mixed precision
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 8, 8, 8)])
+def test_fp32_apply_matches_oracle(dims):
+    """The FP32 operator of a mixed context: within FP32 rounding of the FP64 oracle."""
+    U, W = inputs.stencil_links(dims, seed=3)
+    n = 6 * inputs.lattice_volume(dims)
+    s = _solver(kind="stencil", dims=dims, m0=8.5, kappa=0.3, U=U, W=W, nev=1, m=2, mwin=1, tol=1e-8,
+                precision="mixed")
+    x = inputs.random_vector(n, 0)
+    y = s.apply(torch.from_numpy(x)).cpu().numpy().astype(np.complex128)
+    ref = jsym.stencil_matvec(U, W, dims, 8.5, 0.3, x)
+    assert np.abs(y - ref).max() <= 2e-6 * np.abs(ref).max()
+    s.close()
+
+
+def test_mixed_dense_n200_matches_oracle():
+    w = inputs.WORKLOADS["dense_n200"]
+    A11, A12 = inputs.dense_jsym(w["n"] // 2, w["seed"])
+    mv = lambda x: jsym.dense_matvec(A11, A12, x)
+    ref = tj.trlan_jsym(mv, w["n"], w["nev"], w["m"], w["mwin"], 1e-12)
+    s = _solver(kind="dense", A11=A11, A12=A12, nev=w["nev"], m=w["m"], mwin=w["mwin"], tol=1e-10,
+                precision="mixed")
+    stats = s.solve()
+    ev, X, res = s.pairs()
+    s.close()
+    assert stats["n_matvec_fp32"] > 0 and stats["n_matvec"] > stats["n_matvec_fp32"]
+    _check_pairs(ev, X, mv, 1e-10, ref["evals"], ref["X"])
+
+
+def test_mixed_stencil_8x8x8x8_matches_golden():
+    g = json.load(open(os.path.join(HERE, "golden", "stencil_8x8x8x8.json")))
+    p = g["params"]
+    dims = tuple(p["dims"])
+    U, W = inputs.stencil_links(dims, p["seed"])
+    mv = lambda x: jsym.stencil_matvec(U, W, dims, p["m0"], p["kappa"], x)
+    s = _solver(kind="stencil", dims=dims, m0=p["m0"], kappa=p["kappa"], U=U, W=W, nev=p["nev"], m=p["m"],
+                mwin=p["mwin"], tol=1e-8, precision="mixed")
+    stats = s.solve()
+    ev, X, res = s.pairs()
+    s.close()
+    assert stats["n_matvec_fp32"] > 0
+    _check_pairs(ev, X, mv, 1e-8, np.array(g["evals"]))
+    assert np.all(res < 1e-8)
