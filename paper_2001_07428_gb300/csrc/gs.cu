@@ -27,32 +27,53 @@ constexpr int kColGroups = kGsThreads / 32;
 constexpr int kRedThreads = 128;
 constexpr double kSqrt2 = 1.4142135623730951;
 
+// c_v and c_w for columns 0..j over rows [p0, p1) of this block, written as per-block partials.
+// Warp q takes chunks of 8 consecutive columns (q*8, q*8 + 64, ...); each lane accumulates the
+// 8 x 4 real sums of its rows, then the warp transposes the 32 accumulators through shared memory
+// so that lane k adds up accumulator k: 31 adds per 32 results instead of 5-step shuffle trees
+// per result (on this GPU one FP64 warp instruction holds the FP64 pipe for ~16 cycles).
+constexpr int kDotCols = 8;
+
 template <typename R>
-__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1) {
+__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1, R* red /* [8 warps][32][33] */) {
   using C = cplx<R>;
   const C* V = (const C*)a.V;
   const C* y = (const C*)a.y;
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   const int64_t n = a.n, h = a.h;
-  coef4* out = (coef4*)a.part_dot;
-  for (int i = q; i <= a.j; i += kColGroups) {
-    const C* vi = V + (int64_t)i * n;
-    C cv = mk<R>(0, 0), cw = mk<R>(0, 0);
+  R* wred = red + (size_t)q * 32 * 33;
+  double* out = a.part_dot;
+  for (int c0 = kDotCols * q; c0 <= a.j; c0 += kDotCols * kColGroups) {
+    R acc[kDotCols][4];
+#pragma unroll
+    for (int c = 0; c < kDotCols; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = (R)0;
+    const int ncol = min(kDotCols, a.j + 1 - c0);
     for (int64_t p = p0 + lane; p < p1; p += 32) {
-      const C v1 = vi[p], v2 = vi[h + p], y1 = y[p], y2 = y[h + p];
-      cv = cfmac(v1, y1, cv);
-      cv = cfmac(v2, y2, cv);
-      cw = cfma(v1, y2, cw);
-      C nv2 = v2; nv2.x = -nv2.x; nv2.y = -nv2.y;
-      cw = cfma(nv2, y1, cw);
+      const C y1 = y[p], y2 = y[h + p];
+#pragma unroll
+      for (int c = 0; c < kDotCols; ++c) {
+        if (c < ncol) {
+          const C* vi = V + (int64_t)(c0 + c) * n;
+          const C v1 = vi[p], v2 = vi[h + p];
+          // c_v += conj(v1) y1 + conj(v2) y2 ;  c_w += v1 y2 - v2 y1
+          acc[c][0] = fma(v1.x, y1.x, fma(v1.y, y1.y, fma(v2.x, y2.x, fma(v2.y, y2.y, acc[c][0]))));
+          acc[c][1] = fma(v1.x, y1.y, fma(-v1.y, y1.x, fma(v2.x, y2.y, fma(-v2.y, y2.x, acc[c][1]))));
+          acc[c][2] = fma(v1.x, y2.x, fma(-v1.y, y2.y, fma(-v2.x, y1.x, fma(v2.y, y1.y, acc[c][2]))));
+          acc[c][3] = fma(v1.x, y2.y, fma(v1.y, y2.x, fma(-v2.x, y1.y, fma(-v2.y, y1.x, acc[c][3]))));
+        }
+      }
     }
-    // lane sums in the working precision, block partials in FP64
-    const double s0 = (double)warp_sum(cv.x), s1 = (double)warp_sum(cv.y);
-    const double s2 = (double)warp_sum(cw.x), s3 = (double)warp_sum(cw.y);
-    if (lane == 0) {
-      coef4 c; c.vr = s0; c.vi = s1; c.wr = s2; c.wi = s3;
-      out[(int64_t)i * a.nblk + blockIdx.x] = c;
-    }
+#pragma unroll
+    for (int c = 0; c < kDotCols; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) wred[(4 * c + t) * 33 + lane] = acc[c][t];
+    __syncwarp();
+    R sum = (R)0;
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) sum += wred[lane * 33 + l];
+    __syncwarp();
+    const int c = lane >> 2, t = lane & 3;
+    if (c < ncol) out[((int64_t)(c0 + c) * a.nblk + blockIdx.x) * 4 + t] = (double)sum;
   }
 }
 
@@ -62,6 +83,7 @@ __global__ void __launch_bounds__(kGsThreads)
 gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_part) {
   using C = cplx<R>;
   __shared__ double sh[32];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   double ar = 0.0, ai = 0.0;
   for (int i = threadIdx.x; i < n_alpha_part; i += kGsThreads) {
     ar += alpha_part[i].x;
@@ -99,13 +121,14 @@ gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_pa
   }
   const double nrm = block_sum((double)nrm_r, sh);  // its barriers also publish the y writes to the whole block
   if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
-  dot_body<R>(a, p0, p1);
+  dot_body<R>(a, p0, p1, (R*)dyn_smem);
 }
 
 // Later passes: first finish the test of the previous pass, then the dot products.
 template <typename R>
 __global__ void __launch_bounds__(kGsThreads) gs_dot_kernel(GSArgs a, int pass) {
   __shared__ double sh[32];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ int s_skip;
   StepState* st = a.st;
   if (threadIdx.x == 0) s_skip = st->done;
@@ -130,7 +153,7 @@ __global__ void __launch_bounds__(kGsThreads) gs_dot_kernel(GSArgs a, int pass) 
   }
   const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
   const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, a.h);
-  dot_body<R>(a, p0, p1);
+  dot_body<R>(a, p0, p1, (R*)dyn_smem);
 }
 
 // Reduce the dot partials of every column (one block per column); with `first`, block j+1 also
@@ -345,8 +368,15 @@ int gs_blocks(int64_t h, int* rows_per_block) {
 }
 
 template <typename R>
+constexpr size_t dot_smem() { return (size_t)kColGroups * 32 * 33 * sizeof(R); }
+
+template <typename R>
 cudaError_t launch_gs_first(const GSArgs& a, const double2* alpha_part, int n_alpha_part, cudaStream_t s) {
-  gs_first_kernel<R><<<a.nblk, kGsThreads, 0, s>>>(a, alpha_part, n_alpha_part);
+  if (dot_smem<R>() > 48 * 1024) {  // per device, so set on every launch (cheap)
+    cudaError_t e = cudaFuncSetAttribute(gs_first_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dot_smem<R>());
+    if (e != cudaSuccess) return e;
+  }
+  gs_first_kernel<R><<<a.nblk, kGsThreads, dot_smem<R>(), s>>>(a, alpha_part, n_alpha_part);
   return cudaGetLastError();
 }
 
@@ -363,7 +393,11 @@ cudaError_t launch_gs_update(const GSArgs& a, cudaStream_t s) {
 
 template <typename R>
 cudaError_t launch_gs_dot(const GSArgs& a, int pass, cudaStream_t s) {
-  gs_dot_kernel<R><<<a.nblk, kGsThreads, 0, s>>>(a, pass);
+  if (dot_smem<R>() > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gs_dot_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dot_smem<R>());
+    if (e != cudaSuccess) return e;
+  }
+  gs_dot_kernel<R><<<a.nblk, kGsThreads, dot_smem<R>(), s>>>(a, pass);
   return cudaGetLastError();
 }
 
