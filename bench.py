@@ -292,48 +292,59 @@ def run_gb300(args, rank, world, local_rank):
     # ---- the chosen (mixed-precision) form on the same workload: time and agreement with FP64
     ev64 = np.zeros(w["nev"])
     B.jtrlan_pairs(ctx, 0, ev64.ctypes.data_as(__import__("ctypes").c_void_p), None, None)
-    prm_m = B.params(w["nev"], w["m"], w["mwin"], TOL, precision=B.JTRLAN_MIXED)
-    ctxm = B.jtrlan_create(op, prm_m, stream.cuda_stream)
-    for _ in range(args.warmup):
-        stm = B.jtrlan_solve(ctxm)
-    tm = []
-    for i in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        stm = B.jtrlan_solve(ctxm)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tm.append(e0.elapsed_time(e1) / 1e3)
-        launches += 0
-    evm = np.zeros(w["nev"])
-    B.jtrlan_pairs(ctxm, 0, evm.ctypes.data_as(__import__("ctypes").c_void_p), None, None)
-    B.jtrlan_destroy(ctxm)
-    t_mixed = statistics.mean(tm)
-    mixed = {"value": t_mixed, "unit": "s", "speedup_vs_fp64": round(t_mean / t_mixed, 3),
-             "n_matvec_fp32": stm["n_matvec_fp32"], "n_matvec_fp64": stm["n_matvec"] - stm["n_matvec_fp32"],
-             "n_restarts": stm["n_restarts"], "max_rel_eig_diff_vs_fp64": float(np.max(np.abs(evm - ev64) / np.abs(ev64))),
-             "form": "FP32 phase to max(tol, 1e-5 max|t|), then FP64 from the summed FP32 Ritz vectors"}
+    forms = {"mixed_reorth": (B.JTRLAN_MIXED_REORTH, "FP64 vectors and matvec; reorthogonalisation in compensated "
+                                                     "FP32 (double-float) on a (hi, lo) basis; FP64 alpha/beta, Ritz "
+                                                     "solve, residuals"),
+             "mixed": (B.JTRLAN_MIXED, "FP32 phase (matvec, GS, rotation in FP32) to max(tol, 1e-5 max|t|), then "
+                                       "mixed_reorth from the summed FP32 Ritz vectors")}
+    mixed = {}
+    for name, (prec, desc) in forms.items():
+        ctxm = B.jtrlan_create(op, B.params(w["nev"], w["m"], w["mwin"], TOL, precision=prec), stream.cuda_stream)
+        for _ in range(args.warmup):
+            stm = B.jtrlan_solve(ctxm)
+        tm = []
+        for i in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stm = B.jtrlan_solve(ctxm)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tm.append(e0.elapsed_time(e1) / 1e3)
+        evm = np.zeros(w["nev"])
+        B.jtrlan_pairs(ctxm, 0, evm.ctypes.data_as(__import__("ctypes").c_void_p), None, None)
+        B.jtrlan_destroy(ctxm)
+        t_m = statistics.mean(tm)
+        mixed[name] = {"value": t_m, "unit": "s", "speedup_vs_fp64": round(t_mean / t_m, 3),
+                       "n_matvec_fp32": stm["n_matvec_fp32"], "n_matvec_fp64": stm["n_matvec"] - stm["n_matvec_fp32"],
+                       "n_restarts": stm["n_restarts"],
+                       "max_rel_eig_diff_vs_fp64": float(np.max(np.abs(evm - ev64) / np.abs(ev64))), "form": desc}
+    mixed["chosen"] = min((k for k in forms), key=lambda k: mixed[k]["value"])
 
-    # ---- one profiled solve: per-kernel device time
-    prm_p = B.params(w["nev"], w["m"], w["mwin"], TOL, profile=1)
-    ctxp = B.jtrlan_create(op, prm_p, stream.cuda_stream)
-    flush.zero_()
-    torch.cuda.synchronize()
-    stp = B.jtrlan_solve(ctxp)
-    prof = B.jtrlan_get_profile(ctxp)
-    B.jtrlan_destroy(ctxp)
-    tot_ms = sum(v["ms"] for v in prof.values())
-    kernels = {}
-    for k, v in prof.items():
-        if v["launches"] == 0:
-            continue
-        e = {"ms": round(v["ms"], 3), "launches": v["launches"], "share": round(v["ms"] / tot_ms, 4)}
-        if k in FLOP_PER_UNIT and v["ms"] > 0:
-            e["tflops"] = round(v["work"] * FLOP_PER_UNIT[k] / (v["ms"] * 1e-3) / 1e12, 4)
-        if k in BYTES_PER_UNIT and v["ms"] > 0:
-            e["gbs"] = round(v["work"] * BYTES_PER_UNIT[k] / (v["ms"] * 1e-3) / 1e9, 1)
-        kernels[k] = e
+    # ---- one profiled solve per form: per-kernel device time
+    def profiled(precision):
+        ctxp = B.jtrlan_create(op, B.params(w["nev"], w["m"], w["mwin"], TOL, precision=precision, profile=1),
+                               stream.cuda_stream)
+        flush.zero_()
+        torch.cuda.synchronize()
+        B.jtrlan_solve(ctxp)
+        prof = B.jtrlan_get_profile(ctxp)
+        B.jtrlan_destroy(ctxp)
+        tot_ms = sum(v["ms"] for v in prof.values())
+        out = {}
+        for k, v in prof.items():
+            if v["launches"] == 0:
+                continue
+            e = {"ms": round(v["ms"], 3), "launches": v["launches"], "share": round(v["ms"] / tot_ms, 4)}
+            if k in FLOP_PER_UNIT and v["ms"] > 0:
+                e["tflops"] = round(v["work"] * FLOP_PER_UNIT[k] / (v["ms"] * 1e-3) / 1e12, 4)
+            if k in BYTES_PER_UNIT and v["ms"] > 0:
+                e["gbs"] = round(v["work"] * BYTES_PER_UNIT[k] / (v["ms"] * 1e-3) / 1e9, 1)
+            out[k] = e
+        return out
+
+    kernels = profiled(B.JTRLAN_FP64)
+    mixed["kernels_" + mixed["chosen"]] = profiled(forms[mixed["chosen"]][0])
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     hbm_peak, hbm_src = measured_peaks()
     if "tflops" in kernels[dom]:

@@ -45,7 +45,7 @@ typedef enum {
 enum { JTRLAN_DENSE = 0, JTRLAN_STENCIL4D = 1 };     /* jtrlan_operator.kind   */
 enum { JTRLAN_C128 = 0, JTRLAN_C64 = 1 };            /* jtrlan_operator.dtype  */
 enum { JTRLAN_SMALLEST = 0, JTRLAN_LARGEST = 1 };    /* jtrlan_params.which    */
-enum { JTRLAN_FP64 = 0, JTRLAN_MIXED = 1 };          /* jtrlan_params.precision */
+enum { JTRLAN_FP64 = 0, JTRLAN_MIXED = 1, JTRLAN_MIXED_REORTH = 2 };  /* jtrlan_params.precision */
 
 /* The operator A in the block form of eq. (4).
  *
@@ -82,10 +82,14 @@ typedef struct {
  *   (eq. (29)), 0 <= mwin.
  *   tol: convergence threshold on ||A x - lambda x|| with ||x|| = 1 (Algorithm 1, normal mode).
  *   which: JTRLAN_SMALLEST (smallest algebraic) or JTRLAN_LARGEST.
- *   precision: JTRLAN_FP64 -- plain FP64 arithmetic throughout.  JTRLAN_MIXED -- an FP32 phase
- *     (matvec, Gram-Schmidt and basis rotation in FP32; alpha/beta accumulation, the Ritz solve and
- *     the residual norms in FP64) run to max(tol, 1e-5 max|t|), then FP64 TRLAN-JSYM started from
- *     the normalised sum of the FP32 Ritz vectors run to tol.  Results are FP64 in both modes.
+ *   precision: JTRLAN_FP64 -- plain FP64 arithmetic throughout.
+ *     JTRLAN_MIXED_REORTH -- FP64 vectors, matvec, alpha/beta, Ritz solve and residuals; the
+ *       reorthogonalisation against V and W = J V^* is classical Gram-Schmidt done twice with its
+ *       inner products in FP32 (first update applied in FP64, second correction formed in FP32).
+ *     JTRLAN_MIXED -- an FP32 phase (matvec, Gram-Schmidt and rotation in FP32; alpha/beta, Ritz
+ *       solve and residual norms in FP64) run to max(tol, 1e-5 max|t|), then the JTRLAN_MIXED_REORTH
+ *       solve started from the normalised sum of the FP32 Ritz vectors, run to tol.
+ *     Results are FP64 in every mode.
  *   max_restarts: bound on outer iterations (N_conv); 0 selects 1000.
  *   gs_max_passes: bound on Gram-Schmidt passes per Lanczos step (Algorithm 2 has none);
  *     0 selects 3.
@@ -151,7 +155,7 @@ jtrlan_status jtrlan_create(const jtrlan_operator* op, const jtrlan_params* para
                             void* cuda_stream, jtrlan_ctx** out);
 
 /* y = A x in the canonical layout, both device pointers of n complex numbers: double2 for a
- * JTRLAN_FP64 context, float2 (the FP32 operator of the first phase) for JTRLAN_MIXED.
+ * JTRLAN_FP64 context, float2 (the FP32 operator) for the two mixed modes.
  * Enqueued on the context stream; no sync.
  * This is the Algorithm 2 product A v_j.  Errors: JTRLAN_EINVAL (null), JTRLAN_ECUDA. */
 jtrlan_status jtrlan_apply(jtrlan_ctx* ctx, const void* x, void* y);

@@ -18,7 +18,7 @@ JTRLAN_EBREAKDOWN, JTRLAN_ENOCONV, JTRLAN_ETIMEOUT, JTRLAN_ESTATE = 5, 6, 7, 8
 JTRLAN_DENSE, JTRLAN_STENCIL4D = 0, 1
 JTRLAN_C128, JTRLAN_C64 = 0, 1
 JTRLAN_SMALLEST, JTRLAN_LARGEST = 0, 1
-JTRLAN_FP64, JTRLAN_MIXED = 0, 1
+JTRLAN_FP64, JTRLAN_MIXED, JTRLAN_MIXED_REORTH = 0, 1, 2
 
 EXPORTED = ["jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
             "jtrlan_residual_norms_noalloc", "jtrlan_destroy", "jtrlan_status_string", "jtrlan_last_error"]

@@ -92,10 +92,12 @@ struct Profiler {
 // Operator copy and Krylov basis in one working precision.
 struct Phase {
   OpDev op{};
-  void* V = nullptr;      // n x (m + 1)
-  void* Vtmp = nullptr;   // n x kk (rotation target)
+  void* V = nullptr;      // n x (m + 1); float4 (hi, lo) pairs in a double-float phase
+  void* Vtmp = nullptr;   // n x kk (rotation target; FP64 in a double-float phase)
   void* y = nullptr;      // the vector being built
-  size_t cs = 0;          // bytes per complex number
+  void* x = nullptr;      // double-float phase: FP64 copy of v_j (the matvec input)
+  bool df = false;        // basis stored as compensated FP32 pairs
+  size_t cs = 0;          // bytes per complex number of V
   double* alpha_part = nullptr;
   double* resid_part = nullptr;
   int mv_nblk = 0;
@@ -113,7 +115,7 @@ struct jtrlan_ctx {
   bool mixed = false;              // JTRLAN_MIXED: an FP32 phase, then the FP64 phase
   std::vector<void*> owned;        // device allocations
   std::vector<void*> owned_host;   // pinned host allocations
-  Phase p64, p32;                  // per-precision operator copy and basis buffers
+  Phase p64, p32, pdf;             // FP64, FP32 and double-float phases (allocated as the mode needs)
   double* T = nullptr;
   double* lam = nullptr;
   double* Z = nullptr;
@@ -226,7 +228,8 @@ jtrlan_status validate(const jtrlan_operator* op, const jtrlan_params* p) {
   if (p->mwin < 0) return fail(JTRLAN_EINVAL, "need mwin >= 0");
   if (!(p->tol > 0.0)) return fail(JTRLAN_EINVAL, "need tol > 0");
   if (p->which != JTRLAN_SMALLEST && p->which != JTRLAN_LARGEST) return fail(JTRLAN_EINVAL, "unknown which");
-  if (p->precision != JTRLAN_FP64 && p->precision != JTRLAN_MIXED) return fail(JTRLAN_EINVAL, "unknown precision");
+  if (p->precision != JTRLAN_FP64 && p->precision != JTRLAN_MIXED && p->precision != JTRLAN_MIXED_REORTH)
+    return fail(JTRLAN_EINVAL, "unknown precision");
   if (p->gs_max_passes < 0 || p->gs_max_passes > 7) return fail(JTRLAN_EINVAL, "gs_max_passes must be 0..7");
   if (p->max_restarts < 0) return fail(JTRLAN_EINVAL, "max_restarts must be >= 0");
   return JTRLAN_OK;
@@ -248,7 +251,7 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   c->kk = std::min(prm->nev + prm->mwin, prm->m - 1);
   c->max_restarts = prm->max_restarts ? prm->max_restarts : 1000;
   c->gs_passes = prm->gs_max_passes ? prm->gs_max_passes : 3;
-  c->mixed = prm->precision == JTRLAN_MIXED;
+  c->mixed = prm->precision != JTRLAN_FP64;   // both mixed forms keep the FP32 operator
   OpDev& o = c->p64.op;
   o.kind = op->kind;
   o.n = c->n;
@@ -282,7 +285,14 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
     JT_TRY(c->dalloc(&ph.resid_part, (size_t)ph.mv_nblk * c->nev * sizeof(double)));
     return JTRLAN_OK;
   };
-  JT_TRY(make_phase(c->p64, sizeof(double2)));
+  if (!c->mixed) {
+    JT_TRY(make_phase(c->p64, sizeof(double2)));
+  } else {  // double-float phase on the FP64 operator
+    c->pdf.op = o;
+    c->pdf.df = true;
+    JT_TRY(make_phase(c->pdf, sizeof(float4)));
+    JT_TRY(c->dalloc(&c->pdf.x, (size_t)c->n * sizeof(double2)));
+  }
   if (c->mixed) {  // the FP32 operator: links re-laid out structure-of-arrays, or FP32 dense blocks
     OpDev& q = c->p32.op;
     q = o;
@@ -302,7 +312,11 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
       JT_CUDA(launch_c128_to_c64(o.a12, b, c->h * c->h, c->stream));
       q.a11 = a; q.a12 = b;
     }
-    JT_TRY(make_phase(c->p32, sizeof(float2)));
+    if (prm->precision == JTRLAN_MIXED) {
+      JT_TRY(make_phase(c->p32, sizeof(float2)));
+    } else {
+      c->p32.mv_nblk = matvec_blocks(q);
+    }
   }
   JT_TRY(c->dalloc(&c->T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
   JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));
@@ -329,10 +343,11 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   JT_TRY(c->halloc(&c->h_order, (size_t)c->nev * sizeof(int)));
   JT_TRY(c->halloc(&c->h_misc, 16 * sizeof(double)));
   if (prm->check_jsym) {  // Lemma 1: (J v^*)^H A v = 0 for any v
-    JT_CUDA(launch_fill_random<double>(c->p64.Vtmp, c->n, 0x5eed1234ull, c->stream));
-    JT_CUDA(launch_matvec<double>(o, (const double2*)c->p64.Vtmp, (double2*)c->p64.y, MV_PLAIN, nullptr, nullptr,
+    Phase& ph = c->mixed ? c->pdf : c->p64;   // both have FP64 Vtmp and y
+    JT_CUDA(launch_fill_random<double>(ph.Vtmp, c->n, 0x5eed1234ull, c->stream));
+    JT_CUDA(launch_matvec<double>(o, (const double2*)ph.Vtmp, (double2*)ph.y, MV_PLAIN, nullptr, nullptr,
                                   nullptr, 0, 0, nullptr, c->stream));
-    JT_CUDA(launch_jsym_check<double>(c->p64.Vtmp, c->p64.y, c->h, c->d_misc, c->stream));
+    JT_CUDA(launch_jsym_check<double>(ph.Vtmp, ph.y, c->h, c->d_misc, c->stream));
     JT_CUDA(cudaMemcpyAsync(c->h_misc, c->d_misc, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     JT_CUDA(cudaStreamSynchronize(c->stream));
     const double wAv = std::hypot(c->h_misc[0], c->h_misc[1]);
@@ -385,19 +400,34 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
   *icnv_out = 0;
   for (int restart = 0; restart < max_restarts; ++restart) {
     // ---- Algorithm 2: m - k Lanczos steps, no host synchronisation inside
+    if (ph.df) LAUNCH(K_OTHER, launch_fp64_from_df(col(ph.V, n, k, cs), ph.x, n, s));   // v_k in FP64
     for (int j = k; j < m; ++j) {
-      LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)col(ph.V, n, j, cs), (C*)ph.y, MV_ALPHA, ph.alpha_part,
+      const void* vj = ph.df ? ph.x : col(ph.V, n, j, cs);
+      LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)vj, (C*)ph.y, MV_ALPHA, ph.alpha_part,
                                         nullptr, nullptr, 0, 0, nullptr, s));
       a.j = j;
-      LAUNCH(K_GS_FIRST, launch_gs_first<R>(a, (const double2*)ph.alpha_part, ph.mv_nblk, s));
-      LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
-      LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
-      for (int pass = 2; pass <= c->gs_passes; ++pass) {
-        LAUNCH(K_GS_DOT, launch_gs_dot<R>(a, pass, s));
-        LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
+      if (ph.df) {
+        // compensated FP32 reorthogonalisation of an FP64 vector against a (hi, lo) basis; see gsdf.cu
+        LAUNCH(K_GS_FIRST, launch_gsdf_first(a, ph.x, (const double2*)ph.alpha_part, ph.mv_nblk, s));
+        LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
+        LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
+        for (int pass = 2; pass <= c->gs_passes; ++pass) {
+          LAUNCH(K_GS_DOT, launch_gsdf_dot(a, pass, s));
+          LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
+          LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
+        }
+        LAUNCH(K_GS_NORMALIZE, launch_gsdf_normalize(a, ph.x, s));
+      } else {
+        LAUNCH(K_GS_FIRST, launch_gs_first<R>(a, (const double2*)ph.alpha_part, ph.mv_nblk, s));
+        LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
         LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
+        for (int pass = 2; pass <= c->gs_passes; ++pass) {
+          LAUNCH(K_GS_DOT, launch_gs_dot<R>(a, pass, s));
+          LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
+          LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
+        }
+        LAUNCH(K_GS_NORMALIZE, launch_gs_normalize<R>(a, s));
       }
-      LAUNCH(K_GS_NORMALIZE, launch_gs_normalize<R>(a, s));
     }
     stt.n_matvec += m - k;
     c->work[K_MATVEC] += (double)(m - k) * mv_units;
@@ -407,7 +437,10 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     c->nl[K_RITZ] += 1;  // two kernels: bisection + inverse iteration, checks
     LAUNCH(K_RITZ_FALLBACK, launch_ritz_fallback(c->T, ldt, m, c->prm.which, c->lam, c->Z, c->work_ritz(),
                                                  c->ritz_flags, &c->st->n_ritz_fallbacks, s));
-    LAUNCH(K_ROTATE, launch_rotate<R>(ph.V, n, m, c->Z, kk, ph.Vtmp, s));
+    if (ph.df)
+      LAUNCH(K_ROTATE, launch_rotate_df(ph.V, n, m, c->Z, kk, ph.Vtmp, s));
+    else
+      LAUNCH(K_ROTATE, launch_rotate<R>(ph.V, n, m, c->Z, kk, ph.Vtmp, s));
     c->work[K_ROTATE] += 2.0 * (double)n * m * kk;
     LAUNCH(K_OTHER, launch_report(c->lam, c->Z, m, c->T, ldt, c->st, c->d_rep, s));
     JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * m + 8) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -466,7 +499,10 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     if (icnv == nev) {
       for (int i = 0; i < m; ++i) c->h_perm[i] = perm[i];
       JT_CUDA(cudaMemcpyAsync(c->d_perm, c->h_perm, m * sizeof(int), cudaMemcpyHostToDevice, s));
-      LAUNCH(K_SHRINK, launch_shrink<R>(ph.V, ph.Vtmp, n, c->d_perm, nev, m, s));
+      if (ph.df)
+        LAUNCH(K_SHRINK, launch_shrink_df(ph.V, ph.Vtmp, n, c->d_perm, nev, m, s));
+      else
+        LAUNCH(K_SHRINK, launch_shrink<R>(ph.V, ph.Vtmp, n, c->d_perm, nev, m, s));
       JT_CUDA(cudaStreamSynchronize(s));
       JT_CUDA(c->prof.harvest());
       break;
@@ -486,7 +522,10 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     JT_CUDA(cudaMemcpyAsync(c->T, c->h_T, (size_t)ldt * ldt * sizeof(double), cudaMemcpyHostToDevice, s));
     JT_CUDA(cudaMemcpyAsync(&c->st->tmax, c->h_misc, sizeof(double), cudaMemcpyHostToDevice, s));
     JT_CUDA(cudaMemcpyAsync(c->d_perm, c->h_perm, m * sizeof(int), cudaMemcpyHostToDevice, s));
-    LAUNCH(K_SHRINK, launch_shrink<R>(ph.V, ph.Vtmp, n, c->d_perm, k, m, s));  // and v_{k+1} = v_{m+1}
+    if (ph.df)
+      LAUNCH(K_SHRINK, launch_shrink_df(ph.V, ph.Vtmp, n, c->d_perm, k, m, s));  // and v_{k+1} = v_{m+1}
+    else
+      LAUNCH(K_SHRINK, launch_shrink<R>(ph.V, ph.Vtmp, n, c->d_perm, k, m, s));
   }
   // carry the device counters of this phase into the next one
   c->work_base[0] = c->work[K_GS_FIRST];
@@ -514,13 +553,13 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
   int icnv = 0;
   jtrlan_status st = JTRLAN_OK;
   if (c->prm.v1 && c->opd.dtype != JTRLAN_C128) return fail(JTRLAN_EINVAL, "v1 must be complex128");
-  if (c->mixed) {
+  if (c->prm.precision == JTRLAN_MIXED) {
     // FP32 phase: matvec, Gram-Schmidt and rotation in FP32, alpha/beta and Ritz in FP64, to the
     // tolerance max(tol, 1e-5 max|t|) that FP32 vectors can certify.
     Phase& ph = c->p32;
     if (c->prm.v1) {
-      JT_CUDA(cudaMemcpyAsync(c->p64.y, c->prm.v1, (size_t)n * sizeof(double2), cudaMemcpyDefault, s));
-      LAUNCH(K_OTHER, launch_c128_to_c64(c->p64.y, ph.V, n, s));
+      JT_CUDA(cudaMemcpyAsync(c->pdf.y, c->prm.v1, (size_t)n * sizeof(double2), cudaMemcpyDefault, s));
+      LAUNCH(K_OTHER, launch_c128_to_c64(c->pdf.y, ph.V, n, s));
     } else {
       LAUNCH(K_OTHER, launch_fill_ones<float>(ph.V, n, s));
     }
@@ -535,10 +574,13 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
     stt.n_gs_passes += s32.n_gs_passes;
     stt.n_restarts_fp32 = s32.n_restarts;
     stt.n_restarts += s32.n_restarts;
-    // FP64 phase starts from the normalised sum of the FP32 Ritz vectors (promoted)
-    LAUNCH(K_OTHER, launch_sum_columns(ph.V, n, std::max(icnv, 1), c->p64.V, s));
-    LAUNCH(K_OTHER, launch_normalize_col<double>(c->p64.V, n, c->part_nrm, c->gs_nblk, s));
-    c->nl[K_OTHER] += 1;
+    // the double-float phase starts from the normalised sum of the FP32 Ritz vectors (promoted)
+    LAUNCH(K_OTHER, launch_sum_columns(ph.V, n, std::max(icnv, 1), c->pdf.x, s));
+  } else if (c->mixed) {
+    if (c->prm.v1)
+      JT_CUDA(cudaMemcpyAsync(c->pdf.x, c->prm.v1, (size_t)n * sizeof(double2), cudaMemcpyDefault, s));
+    else
+      LAUNCH(K_OTHER, launch_fill_ones<double>(c->pdf.x, n, s));
   } else {
     if (c->prm.v1) {
       JT_CUDA(cudaMemcpyAsync(c->p64.V, c->prm.v1, (size_t)n * sizeof(double2), cudaMemcpyDefault, s));
@@ -548,8 +590,13 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
       LAUNCH(K_OTHER, launch_fill_ones<double>(c->p64.V, n, s));  // v_1 = 1 / ||1||
     }
   }
+  if (c->mixed) {  // normalise the FP64 start and store it split into the (hi, lo) basis
+    LAUNCH(K_OTHER, launch_normalize_col<double>(c->pdf.x, n, c->part_nrm, c->gs_nblk, s));
+    c->nl[K_OTHER] += 1;
+    LAUNCH(K_OTHER, launch_df_from_fp64(c->pdf.x, c->pdf.V, n, s));
+  }
   jtrlan_stats s64{};
-  st = run_phase<double>(c, c->p64, c->prm.tol, 0.0, c->max_restarts, s64, ev, res, &icnv);
+  st = run_phase<double>(c, c->mixed ? c->pdf : c->p64, c->prm.tol, 0.0, c->max_restarts, s64, ev, res, &icnv);
   stt.n_matvec += s64.n_matvec;
   stt.n_resid_matvec += s64.n_resid_matvec;
   stt.n_gs_passes += s64.n_gs_passes;
@@ -626,11 +673,17 @@ jtrlan_status jtrlan_pairs(jtrlan_ctx* c, int with_partners, double* evals, void
                      (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
     cudaGetLastError();
     if (dev) {
-      JT_CUDA(launch_gather_pairs<double>(c->p64.V, c->n, c->d_order, nev, with_partners, evecs, c->stream));
+      if (c->mixed)
+        JT_CUDA(launch_gather_pairs_df(c->pdf.V, c->n, c->d_order, nev, with_partners, evecs, c->stream));
+      else
+        JT_CUDA(launch_gather_pairs<double>(c->p64.V, c->n, c->d_order, nev, with_partners, evecs, c->stream));
     } else {
       void* tmp = nullptr;
       JT_CUDA(cudaMallocAsync(&tmp, bytes, c->stream));
-      JT_CUDA(launch_gather_pairs<double>(c->p64.V, c->n, c->d_order, nev, with_partners, tmp, c->stream));
+      if (c->mixed)
+        JT_CUDA(launch_gather_pairs_df(c->pdf.V, c->n, c->d_order, nev, with_partners, tmp, c->stream));
+      else
+        JT_CUDA(launch_gather_pairs<double>(c->p64.V, c->n, c->d_order, nev, with_partners, tmp, c->stream));
       JT_CUDA(cudaMemcpyAsync(evecs, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
       JT_CUDA(cudaFreeAsync(tmp, c->stream));
     }

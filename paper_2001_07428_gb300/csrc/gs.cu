@@ -34,27 +34,32 @@ constexpr double kSqrt2 = 1.4142135623730951;
 // per result (on this GPU one FP64 warp instruction holds the FP64 pipe for ~16 cycles).
 constexpr int kDotCols = 8;
 
-template <typename R>
-__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1, R* red /* [8 warps][32][33] */) {
+// R: storage type of V and y; P: arithmetic type of the projections (P = float on FP64 data is the
+// mixed form's FP32 inner product).
+template <typename R, typename P = R>
+__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1, P* red /* [8 warps][32][33] */) {
   using C = cplx<R>;
+  using Q = cplx<P>;
   const C* V = (const C*)a.V;
   const C* y = (const C*)a.y;
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   const int64_t n = a.n, h = a.h;
-  R* wred = red + (size_t)q * 32 * 33;
+  P* wred = red + (size_t)q * 32 * 33;
   double* out = a.part_dot;
   for (int c0 = kDotCols * q; c0 <= a.j; c0 += kDotCols * kColGroups) {
-    R acc[kDotCols][4];
+    P acc[kDotCols][4];
 #pragma unroll
-    for (int c = 0; c < kDotCols; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = (R)0;
+    for (int c = 0; c < kDotCols; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = (P)0;
     const int ncol = min(kDotCols, a.j + 1 - c0);
     for (int64_t p = p0 + lane; p < p1; p += 32) {
-      const C y1 = y[p], y2 = y[h + p];
+      const C yy1 = y[p], yy2 = y[h + p];
+      const Q y1 = mk<P>((P)yy1.x, (P)yy1.y), y2 = mk<P>((P)yy2.x, (P)yy2.y);
 #pragma unroll
       for (int c = 0; c < kDotCols; ++c) {
         if (c < ncol) {
           const C* vi = V + (int64_t)(c0 + c) * n;
-          const C v1 = vi[p], v2 = vi[h + p];
+          const C vv1 = vi[p], vv2 = vi[h + p];
+          const Q v1 = mk<P>((P)vv1.x, (P)vv1.y), v2 = mk<P>((P)vv2.x, (P)vv2.y);
           // c_v += conj(v1) y1 + conj(v2) y2 ;  c_w += v1 y2 - v2 y1
           acc[c][0] = fma(v1.x, y1.x, fma(v1.y, y1.y, fma(v2.x, y2.x, fma(v2.y, y2.y, acc[c][0]))));
           acc[c][1] = fma(v1.x, y1.y, fma(-v1.y, y1.x, fma(v2.x, y2.y, fma(-v2.y, y2.x, acc[c][1]))));
@@ -68,7 +73,7 @@ __device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1
 #pragma unroll
       for (int t = 0; t < 4; ++t) wred[(4 * c + t) * 33 + lane] = acc[c][t];
     __syncwarp();
-    R sum = (R)0;
+    P sum = (P)0;
 #pragma unroll 8
     for (int l = 0; l < 32; ++l) sum += wred[lane * 33 + l];
     __syncwarp();
@@ -78,7 +83,7 @@ __device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1
 }
 
 // First pass: alpha from the matvec partials, y -= alpha v_j, b0 partials, then the dot products.
-template <typename R>
+template <typename R, typename P = R>
 __global__ void __launch_bounds__(kGsThreads)
 gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_part) {
   using C = cplx<R>;
@@ -121,7 +126,7 @@ gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_pa
   }
   const double nrm = block_sum((double)nrm_r, sh);  // its barriers also publish the y writes to the whole block
   if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
-  dot_body<R>(a, p0, p1, (R*)dyn_smem);
+  dot_body<R, P>(a, p0, p1, (P*)dyn_smem);
 }
 
 // Later passes: first finish the test of the previous pass, then the dot products.
@@ -367,8 +372,8 @@ int gs_blocks(int64_t h, int* rows_per_block) {
   return (int)((h + rpb - 1) / rpb);
 }
 
-template <typename R>
-constexpr size_t dot_smem() { return (size_t)kColGroups * 32 * 33 * sizeof(R); }
+template <typename P>
+constexpr size_t dot_smem() { return (size_t)kColGroups * 32 * 33 * sizeof(P); }
 
 template <typename R>
 cudaError_t launch_gs_first(const GSArgs& a, const double2* alpha_part, int n_alpha_part, cudaStream_t s) {

@@ -1,0 +1,496 @@
+// gsdf.cu -- the Gram-Schmidt part of Algorithm 2 in compensated FP32 ("double-float") arithmetic,
+// for the mixed-precision forms.
+//
+// On this GPU the FP64 pipe runs at 1/64 of the FP32 rate, and in plain FP64 the reorthogonalisation
+// against V and W = J V^* is bound by it.  Here the basis is stored as pairs of FP32 numbers,
+// v = hi + lo (hi = fl32(v), lo = fl32(v - hi): 48 significant bits), the products use the exact
+// FMA split p + e = a*b (Dekker 1971; e = fma(a, b, -p)), and the sums use Knuth's TwoSum with the
+// rounding errors carried in a second accumulator (the Dot2 scheme of Ogita, Rump & Oishi 2005).
+// The inner products and the update come out with errors of a few 1e-15 relative to ||v|| ||y||,
+// which keeps V^H V = I and V^H W = O at FP64 level; the vector y itself, alpha, beta, the norms,
+// the matvec, the Ritz solve and the residuals stay in FP64.
+//
+// Layout: V4[col * n + i] = {hi.re, hi.im, lo.re, lo.im} (float4); xbuf holds v_j in FP64 for the
+// FP64 matvec.  The kernel sequence and the device-side exit test mirror gs.cu.
+#include "internal.h"
+
+namespace jtr {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kGroups = kThreads / 32;
+constexpr int kCols = 8;
+constexpr double kSqrt2 = 1.4142135623730951;
+
+// ------------------------------------------------------------------ error-free building blocks
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {   // s + e = a + b
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, e) += sign * (ah + al) * (bh + bl), products split exactly, cross terms to first order.
+__device__ __forceinline__ void df_acc(float& s, float& e, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = __fmaf_rn(ah, bh, -p);
+  const float cross = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  float t, te;
+  two_sum(s, p, t, te);
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(te, __fadd_rn(pe, cross)));
+}
+__device__ __forceinline__ void df_sub(float& s, float& e, float ah, float al, float bh, float bl) {
+  df_acc(s, e, -ah, -al, bh, bl);
+}
+
+__device__ __forceinline__ float4 split(double2 v) {
+  const float hx = (float)v.x, hy = (float)v.y;
+  return make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
+}
+__device__ __forceinline__ double2 join(float4 f) {
+  return make_double2((double)f.x + (double)f.z, (double)f.y + (double)f.w);
+}
+
+// ------------------------------------------------------------------ inner products (one pass)
+// c_v,i = sum_p conj(v1) y1 + conj(v2) y2 and c_w,i = sum_p (v1 y2 - v2 y1) for columns 0..j over
+// rows [p0, p1); y has been split into ys (shared, [2][rows]).  Warp q takes chunks of 8 columns;
+// each lane keeps 8 x 4 (sum, error) pairs, combines them to FP64 and the warp transposes them
+// through shared memory so that lane k adds up accumulator k.
+__device__ void dfdot_body(const GSArgs& a, int64_t p0, int64_t p1, const float4* ys, float* red) {
+  const float4* V = (const float4*)a.V;
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int64_t n = a.n, h = a.h, rows = p1 - p0;
+  float* wred_s = red + (size_t)q * 2 * 32 * 33;   // sums, then rounding errors, [32][33] each
+  float* wred_e = wred_s + 32 * 33;
+  for (int c0 = kCols * q; c0 <= a.j; c0 += kCols * kGroups) {
+    float s[kCols][4], e[kCols][4];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) s[c][t] = e[c][t] = 0.f;
+    const int ncol = min(kCols, a.j + 1 - c0);
+    for (int64_t r = lane; r < rows; r += 32) {
+      const float4 y1 = ys[r], y2 = ys[rows + r];
+      const int64_t p = p0 + r;
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) {
+        if (c < ncol) {
+          const float4* vi = V + (int64_t)(c0 + c) * n;
+          const float4 v1 = vi[p], v2 = vi[h + p];
+          // Re c_v: v1.x y1.x + v1.y y1.y + v2.x y2.x + v2.y y2.y
+          df_acc(s[c][0], e[c][0], v1.x, v1.z, y1.x, y1.z);
+          df_acc(s[c][0], e[c][0], v1.y, v1.w, y1.y, y1.w);
+          df_acc(s[c][0], e[c][0], v2.x, v2.z, y2.x, y2.z);
+          df_acc(s[c][0], e[c][0], v2.y, v2.w, y2.y, y2.w);
+          // Im c_v: v1.x y1.y - v1.y y1.x + v2.x y2.y - v2.y y2.x
+          df_acc(s[c][1], e[c][1], v1.x, v1.z, y1.y, y1.w);
+          df_sub(s[c][1], e[c][1], v1.y, v1.w, y1.x, y1.z);
+          df_acc(s[c][1], e[c][1], v2.x, v2.z, y2.y, y2.w);
+          df_sub(s[c][1], e[c][1], v2.y, v2.w, y2.x, y2.z);
+          // Re c_w: v1.x y2.x - v1.y y2.y - v2.x y1.x + v2.y y1.y
+          df_acc(s[c][2], e[c][2], v1.x, v1.z, y2.x, y2.z);
+          df_sub(s[c][2], e[c][2], v1.y, v1.w, y2.y, y2.w);
+          df_sub(s[c][2], e[c][2], v2.x, v2.z, y1.x, y1.z);
+          df_acc(s[c][2], e[c][2], v2.y, v2.w, y1.y, y1.w);
+          // Im c_w: v1.x y2.y + v1.y y2.x - v2.x y1.y - v2.y y1.x
+          df_acc(s[c][3], e[c][3], v1.x, v1.z, y2.y, y2.w);
+          df_acc(s[c][3], e[c][3], v1.y, v1.w, y2.x, y2.z);
+          df_sub(s[c][3], e[c][3], v2.x, v2.z, y1.y, y1.w);
+          df_sub(s[c][3], e[c][3], v2.y, v2.w, y1.x, y1.z);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCols; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        wred_s[(4 * c + t) * 33 + lane] = s[c][t];
+        wred_e[(4 * c + t) * 33 + lane] = e[c][t];
+      }
+    __syncwarp();
+    // lane k adds up accumulator k over the 32 lanes, still compensated; one FP64 conversion
+    float S = 0.f, E = 0.f;
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) {
+      float t, te;
+      two_sum(S, wred_s[lane * 33 + l], t, te);
+      S = t;
+      E = __fadd_rn(E, __fadd_rn(te, wred_e[lane * 33 + l]));
+    }
+    __syncwarp();
+    const int c = lane >> 2, t = lane & 3;
+    if (c < ncol) a.part_dot[((int64_t)(c0 + c) * a.nblk + blockIdx.x) * 4 + t] = (double)S + (double)E;
+  }
+}
+
+// shared-memory layout of the dot kernels: ys [2 * rows_per_block] float4, then the reduction buffer
+__device__ __forceinline__ void split_rows(const GSArgs& a, int64_t p0, int64_t p1, float4* ys) {
+  const double2* y = (const double2*)a.y;
+  const int64_t rows = p1 - p0;
+  for (int64_t r = threadIdx.x; r < rows; r += kThreads) {
+    ys[r] = split(y[p0 + r]);
+    ys[rows + r] = split(y[a.h + p0 + r]);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads)
+gsdf_first_kernel(GSArgs a, const double2* __restrict__ x, const double2* __restrict__ alpha_part, int n_alpha_part) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ double sh[32];
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < n_alpha_part; i += kThreads) {
+    ar += alpha_part[i].x;
+    ai += alpha_part[i].y;
+  }
+  ar = block_sum(ar, sh);
+  ai = block_sum(ai, sh);
+  const int j = a.j;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.T[(int64_t)j * a.ldt + j] = ar;                 // t_{j,j} (its real part)
+    StepState* st = a.st;
+    st->alpha_im = ai;
+    st->done = 0;
+    double tm = fmax(st->tmax, fabs(ar));
+    if (j > 0) tm = fmax(tm, fabs(a.T[(int64_t)j * a.ldt + j - 1]));
+    st->tmax = tm;
+    st->n_passes += 1;
+    st->units_first += (double)(j + 1) * (double)a.h;
+  }
+  double2* y = (double2*)a.y;
+  const int64_t h = a.h;
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+  double nrm = 0.0;
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {   // y -= alpha v_j, exactly in FP64
+    double2 y1 = y[p], y2 = y[h + p];
+    const double2 v1 = x[p], v2 = x[h + p];
+    y1.x -= ar * v1.x; y1.y -= ar * v1.y;
+    y2.x -= ar * v2.x; y2.y -= ar * v2.y;
+    y[p] = y1;
+    y[h + p] = y2;
+    nrm += cabs2(y1) + cabs2(y2);
+  }
+  nrm = block_sum(nrm, sh);
+  if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
+  float4* ys = (float4*)dyn;
+  float* red = (float*)(ys + 2 * a.rows_per_block);
+  split_rows(a, p0, p1, ys);
+  dfdot_body(a, p0, p1, ys, red);
+}
+
+__global__ void __launch_bounds__(kThreads) gsdf_dot_kernel(GSArgs a, int pass) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ double sh[32];
+  __shared__ int s_skip;
+  StepState* st = a.st;
+  if (threadIdx.x == 0) s_skip = st->done;
+  __syncthreads();
+  if (s_skip) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < a.nblk; b += kThreads) s += a.part_nrm[b];
+  const double nrm_prev = sqrt(block_sum(s, sh));   // b1 after pass - 1
+  const double ref = st->nrm[pass - 2];              // b0 before pass - 1
+  if (kSqrt2 * nrm_prev > ref) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->nrm[pass - 1] = nrm_prev;
+      st->beta = nrm_prev;
+      st->done = 1;
+    }
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->nrm[pass - 1] = nrm_prev;
+    st->n_passes += 1;
+    st->units_dot += (double)(a.j + 1) * (double)a.h;
+  }
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, a.h);
+  float4* ys = (float4*)dyn;
+  float* red = (float*)(ys + 2 * a.rows_per_block);
+  split_rows(a, p0, p1, ys);
+  dfdot_body(a, p0, p1, ys, red);
+}
+
+// y -= V c_v + W c_w: the correction is accumulated per row in compensated FP32 over this warp's
+// columns, the eight warps' pieces are added in FP64, and y is updated in FP64.
+__global__ void __launch_bounds__(kThreads) gsdf_update_kernel(GSArgs a) {
+  extern __shared__ float4 scf[];                       // per column: {cv hi/lo}, {cw hi/lo}
+  __shared__ float red_s[kGroups][32][4], red_e[kGroups][32][4];
+  __shared__ double sh[32];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = a.st->done;
+  __syncthreads();
+  if (s_skip) return;
+  const int j = a.j;
+  for (int i = threadIdx.x; i <= j; i += kThreads) {
+    const coef4 c = a.coef[i];
+    scf[2 * i] = split(make_double2(c.vr, c.vi));
+    scf[2 * i + 1] = split(make_double2(c.wr, c.wi));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.st->units_update += (double)(j + 1) * (double)a.h;
+  __syncthreads();
+  const float4* V = (const float4*)a.V;
+  double2* y = (double2*)a.y;
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int64_t n = a.n, h = a.h;
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+  double nrm = 0.0;
+  for (int64_t pb = p0; pb < p1; pb += 32) {
+    const int64_t p = pb + lane;
+    const bool ok = p < p1;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+    if (ok) {
+      for (int i = q; i <= j; i += kGroups) {
+        const float4 v1 = V[(int64_t)i * n + p], v2 = V[(int64_t)i * n + h + p];
+        const float4 cv = scf[2 * i], cw = scf[2 * i + 1];
+        // y1 correction: v1 c_v - conj(v2) c_w
+        df_acc(s[0], e[0], v1.x, v1.z, cv.x, cv.z);  df_sub(s[0], e[0], v1.y, v1.w, cv.y, cv.w);
+        df_sub(s[0], e[0], v2.x, v2.z, cw.x, cw.z);  df_sub(s[0], e[0], v2.y, v2.w, cw.y, cw.w);
+        df_acc(s[1], e[1], v1.x, v1.z, cv.y, cv.w);  df_acc(s[1], e[1], v1.y, v1.w, cv.x, cv.z);
+        df_sub(s[1], e[1], v2.x, v2.z, cw.y, cw.w);  df_acc(s[1], e[1], v2.y, v2.w, cw.x, cw.z);
+        // y2 correction: v2 c_v + conj(v1) c_w
+        df_acc(s[2], e[2], v2.x, v2.z, cv.x, cv.z);  df_sub(s[2], e[2], v2.y, v2.w, cv.y, cv.w);
+        df_acc(s[2], e[2], v1.x, v1.z, cw.x, cw.z);  df_acc(s[2], e[2], v1.y, v1.w, cw.y, cw.w);
+        df_acc(s[3], e[3], v2.x, v2.z, cv.y, cv.w);  df_acc(s[3], e[3], v2.y, v2.w, cv.x, cv.z);
+        df_acc(s[3], e[3], v1.x, v1.z, cw.y, cw.w);  df_sub(s[3], e[3], v1.y, v1.w, cw.x, cw.z);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      red_s[q][lane][t] = s[t];
+      red_e[q][lane][t] = e[t];
+    }
+    __syncthreads();
+    if (q == 0 && ok) {
+      double c[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {   // the eight column groups, still compensated; one conversion
+        float S = red_s[0][lane][t], E = red_e[0][lane][t];
+#pragma unroll
+        for (int g = 1; g < kGroups; ++g) {
+          float u, ue;
+          two_sum(S, red_s[g][lane][t], u, ue);
+          S = u;
+          E = __fadd_rn(E, __fadd_rn(ue, red_e[g][lane][t]));
+        }
+        c[t] = (double)S + (double)E;
+      }
+      double2 y1 = y[p], y2 = y[h + p];
+      y1.x -= c[0]; y1.y -= c[1];
+      y2.x -= c[2]; y2.y -= c[3];
+      y[p] = y1;
+      y[h + p] = y2;
+      nrm += cabs2(y1) + cabs2(y2);
+    }
+    __syncthreads();
+  }
+  nrm = block_sum(nrm, sh);
+  if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
+}
+
+// v_{j+1} = y / beta stored split into V4[:, j+1] and in FP64 into x (the next matvec input).
+__global__ void __launch_bounds__(kThreads) gsdf_normalize_kernel(GSArgs a, double2* __restrict__ x) {
+  __shared__ double sh[32];
+  StepState* st = a.st;
+  const int done = st->done;
+  double beta;
+  if (done) {
+    beta = st->beta;
+  } else {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < a.nblk; b += kThreads) s += a.part_nrm[b];
+    beta = sqrt(block_sum(s, sh));
+  }
+  const double tmax = st->tmax;
+  const bool brk = !(beta > 1e-14 * fmax(tmax, 1.0));
+  const double inv = brk ? 0.0 : 1.0 / beta;
+  const double2* y = (const double2*)a.y;
+  float4* v = (float4*)a.V + (int64_t)(a.j + 1) * a.n;
+  const int64_t h = a.h;
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
+    const double2 y1 = y[p], y2 = y[h + p];
+    const double2 v1 = make_double2(y1.x * inv, y1.y * inv), v2 = make_double2(y2.x * inv, y2.y * inv);
+    v[p] = split(v1);
+    v[h + p] = split(v2);
+    x[p] = v1;
+    x[h + p] = v2;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int j = a.j;
+    a.T[(int64_t)(j + 1) * a.ldt + j] = beta;
+    if (j + 1 < a.m) a.T[(int64_t)j * a.ldt + j + 1] = beta;
+    if (brk) st->status = 5;
+  }
+}
+
+// ------------------------------------------------------------------ basis conversions
+__global__ void df_from_fp64_kernel(const double2* in, float4* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = split(in[i]);
+}
+__global__ void fp64_from_df_kernel(const float4* in, double2* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = join(in[i]);
+}
+// V4[:, c] = split(Vsrc[:, perm[c]]) for c < k and V4[:, k] = V4[:, m].
+__global__ void shrink_df_kernel(float4* V, const double2* Vsrc, int64_t n, const int* perm, int k, int m) {
+  const int c = blockIdx.y;
+  float4* dst = V + (int64_t)c * n;
+  if (c < k) {
+    const double2* src = Vsrc + (int64_t)perm[c] * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      dst[i] = split(src[i]);
+  } else {
+    const float4* src = V + (int64_t)m * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      dst[i] = src[i];
+  }
+}
+// out[:, c] = V4[:, order[c]] (FP64) and, with partners, out[:, nev + c] = J conj(...).
+__global__ void gather_pairs_df_kernel(const float4* V, int64_t n, const int* order, int nev, int partners,
+                                       double2* out) {
+  const int c = blockIdx.y;
+  const int64_t h = n / 2;
+  const float4* src = V + (int64_t)order[c] * n;
+  double2* dst = out + (int64_t)c * n;
+  double2* dstp = out + (int64_t)(nev + c) * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < h; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 x1 = join(src[i]), x2 = join(src[h + i]);
+    dst[i] = x1;
+    dst[h + i] = x2;
+    if (partners) {
+      dstp[i] = make_double2(-x2.x, x2.y);
+      dstp[h + i] = make_double2(x1.x, -x1.y);
+    }
+  }
+}
+
+// Vout (FP64, 2n x kk real view) = V4 (joined to FP64) * Z, FP64 accumulation.
+__global__ void __launch_bounds__(256)
+rotate_df_kernel(const float4* __restrict__ V, int64_t n, int m, const double* __restrict__ Z, int kk,
+                 double* __restrict__ out) {
+  constexpr int BM = 64, BN = 32, BK = 16;
+  __shared__ double As[BK][BM];
+  __shared__ double Bs[BK][BN];
+  const int64_t rows = 2 * n;
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int col0 = blockIdx.y * BN;
+  const int tr = tid % 16, tc = tid / 16;
+  double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (int k0 = 0; k0 < m; k0 += BK) {
+    for (int e = tid; e < BK * BM; e += 256) {
+      const int kx = e / BM, r = e % BM;
+      const int64_t gr = row0 + r;
+      double val = 0.0;
+      if (gr < rows && k0 + kx < m) {
+        const float4 f = V[(int64_t)(k0 + kx) * n + (gr >> 1)];
+        val = (gr & 1) ? (double)f.y + (double)f.w : (double)f.x + (double)f.z;
+      }
+      As[kx][r] = val;
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      const int kx = e / BN, c = e % BN;
+      Bs[kx][c] = (k0 + kx < m && col0 + c < kk) ? Z[(int64_t)(col0 + c) * m + k0 + kx] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int x = 0; x < BK; ++x) {
+      double av[4], bv[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[x][tr + 16 * i];
+      bv[0] = Bs[x][tc];
+      bv[1] = Bs[x][tc + 16];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0] = fma(av[i], bv[0], acc[i][0]);
+        acc[i][1] = fma(av[i], bv[1], acc[i][1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = row0 + tr + 16 * i;
+    if (gr >= rows) continue;
+#pragma unroll
+    for (int jx = 0; jx < 2; ++jx) {
+      const int gc = col0 + tc + 16 * jx;
+      if (gc < kk) out[(int64_t)gc * rows + gr] = acc[i][jx];
+    }
+  }
+}
+
+inline int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g > 1216 ? 1216 : (g < 1 ? 1 : g));
+}
+
+size_t dot_smem(const GSArgs& a) {
+  return (size_t)2 * a.rows_per_block * sizeof(float4) + (size_t)kGroups * 2 * 32 * 33 * sizeof(float);
+}
+
+}  // namespace
+
+cudaError_t launch_gsdf_first(const GSArgs& a, const void* x, const double2* alpha_part, int n_alpha_part,
+                              cudaStream_t s) {
+  const size_t sm = dot_smem(a);
+  cudaError_t e = cudaFuncSetAttribute(gsdf_first_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  gsdf_first_kernel<<<a.nblk, kThreads, sm, s>>>(a, (const double2*)x, alpha_part, n_alpha_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gsdf_dot(const GSArgs& a, int pass, cudaStream_t s) {
+  const size_t sm = dot_smem(a);
+  cudaError_t e = cudaFuncSetAttribute(gsdf_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  gsdf_dot_kernel<<<a.nblk, kThreads, sm, s>>>(a, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gsdf_update(const GSArgs& a, cudaStream_t s) {
+  gsdf_update_kernel<<<a.nblk, kThreads, (size_t)(a.j + 1) * 2 * sizeof(float4), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gsdf_normalize(const GSArgs& a, void* x, cudaStream_t s) {
+  gsdf_normalize_kernel<<<a.nblk, kThreads, 0, s>>>(a, (double2*)x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_from_fp64(const void* in, void* out, int64_t n, cudaStream_t s) {
+  df_from_fp64_kernel<<<grid_for(n), 256, 0, s>>>((const double2*)in, (float4*)out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_from_df(const void* in, void* out, int64_t n, cudaStream_t s) {
+  fp64_from_df_kernel<<<grid_for(n), 256, 0, s>>>((const float4*)in, (double2*)out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shrink_df(void* V, const void* Vsrc, int64_t n, const int* perm, int k, int m, cudaStream_t s) {
+  dim3 grid(grid_for(n) / 4 + 1, k + 1);
+  shrink_df_kernel<<<grid, 256, 0, s>>>((float4*)V, (const double2*)Vsrc, n, perm, k, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pairs_df(const void* V, int64_t n, const int* order, int nev, int partners, void* out,
+                                   cudaStream_t s) {
+  dim3 grid(grid_for(n / 2) / 4 + 1, nev);
+  gather_pairs_df_kernel<<<grid, 256, 0, s>>>((const float4*)V, n, order, nev, partners, (double2*)out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_df(const void* V, int64_t n, int m, const double* Z, int kk, void* Vout, cudaStream_t s) {
+  dim3 grid((unsigned)((2 * n + 63) / 64), (unsigned)((kk + 31) / 32));
+  rotate_df_kernel<<<grid, 256, 0, s>>>((const float4*)V, n, m, Z, kk, (double*)Vout);
+  return cudaGetLastError();
+}
+
+}  // namespace jtr

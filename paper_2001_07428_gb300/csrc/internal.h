@@ -67,6 +67,21 @@ cudaError_t launch_gs_dot(const GSArgs& a, int pass, cudaStream_t s);
 template <typename R>
 cudaError_t launch_gs_normalize(const GSArgs& a, cudaStream_t s);
 
+// Mixed forms: the same Gram-Schmidt sequence in compensated FP32 ("double-float") arithmetic on a
+// basis stored as float4 {hi.re, hi.im, lo.re, lo.im} (gsdf.cu); y, alpha, beta and norms in FP64.
+// x is the FP64 copy of v_j (the matvec input), rewritten with v_{j+1} by the normalisation.
+cudaError_t launch_gsdf_first(const GSArgs& a, const void* x, const double2* alpha_part, int n_alpha_part,
+                              cudaStream_t s);
+cudaError_t launch_gsdf_dot(const GSArgs& a, int pass, cudaStream_t s);
+cudaError_t launch_gsdf_update(const GSArgs& a, cudaStream_t s);
+cudaError_t launch_gsdf_normalize(const GSArgs& a, void* x, cudaStream_t s);
+cudaError_t launch_df_from_fp64(const void* in, void* out, int64_t n, cudaStream_t s);
+cudaError_t launch_fp64_from_df(const void* in, void* out, int64_t n, cudaStream_t s);
+cudaError_t launch_shrink_df(void* V, const void* Vsrc, int64_t n, const int* perm, int k, int m, cudaStream_t s);
+cudaError_t launch_gather_pairs_df(const void* V, int64_t n, const int* order, int nev, int partners, void* out,
+                                   cudaStream_t s);
+cudaError_t launch_rotate_df(const void* V, int64_t n, int m, const double* Z, int kk, void* Vout, cudaStream_t s);
+
 // Kernel classes for the optional per-kernel profile.
 enum KernelTag {
   K_MATVEC = 0, K_GS_FIRST, K_GS_REDUCE, K_GS_UPDATE, K_GS_DOT, K_GS_NORMALIZE, K_RITZ, K_ROTATE,

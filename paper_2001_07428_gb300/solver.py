@@ -49,8 +49,8 @@ class JTRLan:
             v1p = v1d.data_ptr()
         w = B.JTRLAN_LARGEST if which == "largest" else B.JTRLAN_SMALLEST
         self._keep_v1 = keep[-1] if v1 is not None else None
-        self.mixed = precision == "mixed"
-        prec = B.JTRLAN_MIXED if self.mixed else B.JTRLAN_FP64
+        prec = {"fp64": B.JTRLAN_FP64, "mixed": B.JTRLAN_MIXED, "mixed_reorth": B.JTRLAN_MIXED_REORTH}[precision]
+        self.mixed = prec != B.JTRLAN_FP64
         prm = B.params(nev, m, mwin, tol, which=w, precision=prec, max_restarts=max_restarts,
                        gs_max_passes=gs_max_passes, v1_ptr=v1p, check_jsym=int(check_jsym),
                        profile=int(profile))

@@ -217,31 +217,34 @@ def test_fp32_apply_matches_oracle(dims):
     s.close()
 
 
-def test_mixed_dense_n200_matches_oracle():
+@pytest.mark.parametrize("precision", ["mixed", "mixed_reorth"])
+def test_mixed_dense_n200_matches_oracle(precision):
     w = inputs.WORKLOADS["dense_n200"]
     A11, A12 = inputs.dense_jsym(w["n"] // 2, w["seed"])
     mv = lambda x: jsym.dense_matvec(A11, A12, x)
     ref = tj.trlan_jsym(mv, w["n"], w["nev"], w["m"], w["mwin"], 1e-12)
     s = _solver(kind="dense", A11=A11, A12=A12, nev=w["nev"], m=w["m"], mwin=w["mwin"], tol=1e-10,
-                precision="mixed")
+                precision=precision)
     stats = s.solve()
     ev, X, res = s.pairs()
     s.close()
-    assert stats["n_matvec_fp32"] > 0 and stats["n_matvec"] > stats["n_matvec_fp32"]
+    if precision == "mixed":
+        assert stats["n_matvec_fp32"] > 0 and stats["n_matvec"] > stats["n_matvec_fp32"]
     _check_pairs(ev, X, mv, 1e-10, ref["evals"], ref["X"])
 
 
-def test_mixed_stencil_8x8x8x8_matches_golden():
+@pytest.mark.parametrize("precision", ["mixed", "mixed_reorth"])
+def test_mixed_stencil_8x8x8x8_matches_golden(precision):
     g = json.load(open(os.path.join(HERE, "golden", "stencil_8x8x8x8.json")))
     p = g["params"]
     dims = tuple(p["dims"])
     U, W = inputs.stencil_links(dims, p["seed"])
     mv = lambda x: jsym.stencil_matvec(U, W, dims, p["m0"], p["kappa"], x)
     s = _solver(kind="stencil", dims=dims, m0=p["m0"], kappa=p["kappa"], U=U, W=W, nev=p["nev"], m=p["m"],
-                mwin=p["mwin"], tol=1e-8, precision="mixed")
+                mwin=p["mwin"], tol=1e-8, precision=precision)
     stats = s.solve()
     ev, X, res = s.pairs()
     s.close()
-    assert stats["n_matvec_fp32"] > 0
+    assert (stats["n_matvec_fp32"] > 0) == (precision == "mixed")
     _check_pairs(ev, X, mv, 1e-8, np.array(g["evals"]))
     assert np.all(res < 1e-8)
