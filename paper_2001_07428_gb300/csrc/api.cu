@@ -396,6 +396,7 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
   std::vector<double> res_est(nev), lamv(m), arrow(m);
   std::vector<char> conv(nev);
   std::vector<int> perm(m);
+  std::vector<double> locked_ev, locked_res;   // pairs locked at the previous restart
   int k = 0, icnv = 0;
   *icnv_out = 0;
   for (int restart = 0; restart < max_restarts; ++restart) {
@@ -437,11 +438,20 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     c->nl[K_RITZ] += 1;  // two kernels: bisection + inverse iteration, checks
     LAUNCH(K_RITZ_FALLBACK, launch_ritz_fallback(c->T, ldt, m, c->prm.which, c->lam, c->Z, c->work_ritz(),
                                                  c->ritz_flags, &c->st->n_ritz_fallbacks, s));
-    if (ph.df)
-      LAUNCH(K_ROTATE, launch_rotate_df(ph.V, n, m, c->Z, kk, ph.Vtmp, s));
-    else
-      LAUNCH(K_ROTATE, launch_rotate<R>(ph.V, n, m, c->Z, kk, ph.Vtmp, s));
-    c->work[K_ROTATE] += 2.0 * (double)n * m * kk;
+    // V_m Z, first the nev candidate columns (the rest once k of eq. (29) is known)
+    const size_t tcs = ph.df ? sizeof(double2) : cs;   // element size of Vtmp
+    auto rotate_cols = [&](int c0, int ncols) -> jtrlan_status {
+      if (ncols <= 0) return JTRLAN_OK;
+      void* out = (char*)ph.Vtmp + (size_t)c0 * n * tcs;
+      const double* Zc = c->Z + (size_t)c0 * m;
+      if (ph.df)
+        LAUNCH(K_ROTATE, launch_rotate_df(ph.V, n, m, Zc, ncols, out, s));
+      else
+        LAUNCH(K_ROTATE, launch_rotate<R>(ph.V, n, m, Zc, ncols, out, s));
+      c->work[K_ROTATE] += 2.0 * (double)n * m * ncols;
+      return JTRLAN_OK;
+    };
+    JT_TRY(rotate_cols(0, nev));
     LAUNCH(K_OTHER, launch_report(c->lam, c->Z, m, c->T, ldt, c->st, c->d_rep, s));
     JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * m + 8) * sizeof(double), cudaMemcpyDeviceToHost, s));
     JT_CUDA(cudaStreamSynchronize(s));
@@ -461,11 +471,26 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
       arrow[i] = beta_m * c->h_rep[m + i];   // t_{m+1,i} = t_{m+1,m} z_{m,i}
     }
     int ncand = 0;
+    std::vector<char> reused(nev, 0);
     for (int i = 0; i < nev; ++i) {
       ev[i] = lamv[i];
       res_est[i] = std::fabs(arrow[i]);
       conv[i] = 0;                            // is_convd reset every outer iteration
-      if (res_est[i] < tol_ph) { c->h_cand[ncand] = i; c->h_candlam[ncand] = ev[i]; ++ncand; }
+      if (!(res_est[i] < tol_ph)) continue;
+      // A pair locked at the previous restart is decoupled in T-bar (t_{m+1,i} = 0), so the
+      // Rayleigh-Ritz step returns it unchanged: keep its verified residual instead of another
+      // product (reading R6b).
+      int hit = -1;
+      if (res_est[i] < 1e-3 * tol_ph)
+        for (size_t q = 0; q < locked_ev.size(); ++q)
+          if (std::fabs(ev[i] - locked_ev[q]) <= 1e-12 * std::max(1.0, std::fabs(ev[i]))) { hit = (int)q; break; }
+      if (hit >= 0) {
+        res[i] = locked_res[hit];
+        conv[i] = 1;
+        reused[i] = 1;
+        continue;
+      }
+      c->h_cand[ncand] = i; c->h_candlam[ncand] = ev[i]; ++ncand;
     }
     if (ncand > 0) {  // true residuals ||A v_i - ev_i v_i|| of the candidates
       JT_CUDA(cudaMemcpyAsync(c->d_cand, c->h_cand, ncand * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -495,6 +520,8 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     for (int i = 0; i < nev; ++i) { ev2[i] = ev[perm[i]]; res2[i] = res[perm[i]]; }
     ev = ev2; res = res2; lamv = lam2; arrow = arrow2;
     for (int i = 0; i < icnv; ++i) arrow[i] = 0.0;   // decouple the converged subspace
+    locked_ev.assign(ev.begin(), ev.begin() + icnv);
+    locked_res.assign(res.begin(), res.begin() + icnv);
     *icnv_out = icnv;
     if (icnv == nev) {
       for (int i = 0; i < m; ++i) c->h_perm[i] = perm[i];
@@ -509,6 +536,7 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     }
     // ---- shrink to k + 1 (eq. (29)); T-bar = diag(lambda_1..k) with the arrow in row k+1
     k = std::min(icnv + c->mwin, m - 1);
+    JT_TRY(rotate_cols(nev, k - nev));   // the kept columns beyond the candidates
     std::memset(c->h_T, 0, (size_t)ldt * ldt * sizeof(double));
     double tm = 0.0;
     for (int i = 0; i < k; ++i) {

@@ -370,46 +370,57 @@ __global__ void gather_pairs_df_kernel(const float4* V, int64_t n, const int* or
   }
 }
 
-// Vout (FP64, 2n x kk real view) = V4 (joined to FP64) * Z, FP64 accumulation.
+// Vout (FP64, 2n x kk real view) = V4 * Z in compensated FP32: V is already (hi, lo), Z is split
+// into (hi, lo) as it is staged, every multiply-add is df_acc, and each output is (sum + error)
+// converted once to FP64.  The restart rotation is the one dense contraction of the method; on the
+// FP32 pipes it runs at several times the FP64 rate with FP64-level accuracy (K = m <= 1023).
 __global__ void __launch_bounds__(256)
 rotate_df_kernel(const float4* __restrict__ V, int64_t n, int m, const double* __restrict__ Z, int kk,
                  double* __restrict__ out) {
   constexpr int BM = 64, BN = 32, BK = 16;
-  __shared__ double As[BK][BM];
-  __shared__ double Bs[BK][BN];
+  __shared__ float2 As[BK][BM];      // (hi, lo) of the real view of V
+  __shared__ float2 Bs[BK][BN];      // (hi, lo) of Z
   const int64_t rows = 2 * n;
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * BM;
   const int col0 = blockIdx.y * BN;
-  const int tr = tid % 16, tc = tid / 16;
-  double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  const int tr = tid % 16, tc = tid / 16;   // rows tr + 16 i (i < 4), cols tc + 16 j (j < 2)
+  float s[4][2], e[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s[i][0] = s[i][1] = e[i][0] = e[i][1] = 0.f;
   for (int k0 = 0; k0 < m; k0 += BK) {
-    for (int e = tid; e < BK * BM; e += 256) {
-      const int kx = e / BM, r = e % BM;
+    for (int q = tid; q < BK * BM; q += 256) {
+      const int kx = q / BM, r = q % BM;
       const int64_t gr = row0 + r;
-      double val = 0.0;
+      float2 val = make_float2(0.f, 0.f);
       if (gr < rows && k0 + kx < m) {
         const float4 f = V[(int64_t)(k0 + kx) * n + (gr >> 1)];
-        val = (gr & 1) ? (double)f.y + (double)f.w : (double)f.x + (double)f.z;
+        val = (gr & 1) ? make_float2(f.y, f.w) : make_float2(f.x, f.z);
       }
       As[kx][r] = val;
     }
-    for (int e = tid; e < BK * BN; e += 256) {
-      const int kx = e / BN, c = e % BN;
-      Bs[kx][c] = (k0 + kx < m && col0 + c < kk) ? Z[(int64_t)(col0 + c) * m + k0 + kx] : 0.0;
+    for (int q = tid; q < BK * BN; q += 256) {
+      const int kx = q / BN, c = q % BN;
+      float2 val = make_float2(0.f, 0.f);
+      if (k0 + kx < m && col0 + c < kk) {
+        const double z = Z[(int64_t)(col0 + c) * m + k0 + kx];
+        const float zh = (float)z;
+        val = make_float2(zh, (float)(z - (double)zh));
+      }
+      Bs[kx][c] = val;
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 4
     for (int x = 0; x < BK; ++x) {
-      double av[4], bv[2];
+      float2 av[4], bv[2];
 #pragma unroll
       for (int i = 0; i < 4; ++i) av[i] = As[x][tr + 16 * i];
       bv[0] = Bs[x][tc];
       bv[1] = Bs[x][tc + 16];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        acc[i][0] = fma(av[i], bv[0], acc[i][0]);
-        acc[i][1] = fma(av[i], bv[1], acc[i][1]);
+        df_acc(s[i][0], e[i][0], av[i].x, av[i].y, bv[0].x, bv[0].y);
+        df_acc(s[i][1], e[i][1], av[i].x, av[i].y, bv[1].x, bv[1].y);
       }
     }
     __syncthreads();
@@ -421,7 +432,7 @@ rotate_df_kernel(const float4* __restrict__ V, int64_t n, int m, const double* _
 #pragma unroll
     for (int jx = 0; jx < 2; ++jx) {
       const int gc = col0 + tc + 16 * jx;
-      if (gc < kk) out[(int64_t)gc * rows + gr] = acc[i][jx];
+      if (gc < kk) out[(int64_t)gc * rows + gr] = (double)s[i][jx] + (double)e[i][jx];
     }
   }
 }
