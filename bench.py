@@ -151,6 +151,41 @@ def cpu_baseline(name, full_products, restarts=4):
                       f"products A v, {d['seconds']:.1f} s), scaled by the product count"}
 
 
+# ---------------------------------------------------------------- the mixed form where it is quoted
+def mixed_at_16(B, torch, stream, flush):
+    """One timed solve each of plain FP64 and the double-float mixed form on the 16^4 workload
+    (n = 393,216, nev = 50, m = 120, mwin = 60), after one untimed warm-up solve of each."""
+    import ctypes
+    w = inputs.WORKLOADS["stencil_16x16x16x16"]
+    dims = w["dims"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    U, W = inputs.stencil_links(dims, w["seed"])
+    Ud, Wd = torch.from_numpy(U).to(dev), torch.from_numpy(W).to(dev)
+    op = B.stencil_operator(dims, w["m0"], w["kappa"], Ud.data_ptr(), Wd.data_ptr())
+    out = {"workload": "stencil_16x16x16x16", "n": 6 * inputs.lattice_volume(dims), "nev": w["nev"], "m": w["m"],
+           "mwin": w["mwin"], "tol": TOL}
+    evs = {}
+    for name, prec in (("fp64", B.JTRLAN_FP64), ("mixed_reorth", B.JTRLAN_MIXED_REORTH)):
+        ctx = B.jtrlan_create(op, B.params(w["nev"], w["m"], w["mwin"], TOL, precision=prec), stream.cuda_stream)
+        B.jtrlan_solve(ctx)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = B.jtrlan_solve(ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ev = np.zeros(w["nev"])
+        res = np.zeros(w["nev"])
+        B.jtrlan_pairs(ctx, 0, ev.ctypes.data_as(ctypes.c_void_p), None, res.ctypes.data_as(ctypes.c_void_p))
+        B.jtrlan_destroy(ctx)
+        evs[name] = ev
+        out[name] = {"value": e0.elapsed_time(e1) / 1e3, "unit": "s", "n_matvec": st["n_matvec"],
+                     "n_restarts": st["n_restarts"], "max_residual": float(res.max())}
+    out["speedup_vs_fp64"] = round(out["fp64"]["value"] / out["mixed_reorth"]["value"], 3)
+    out["max_rel_eig_diff_vs_fp64"] = float(np.max(np.abs(evs["mixed_reorth"] - evs["fp64"]) / np.abs(evs["fp64"])))
+    return out
+
+
 # ---------------------------------------------------------------- FP32 stencil matvec vs HBM
 STENCIL_LATTICES = {"16x16x16x16": (16, 16, 16, 16), "24x24x24x48": (24, 24, 24, 48)}
 
@@ -345,6 +380,8 @@ def run_gb300(args, rank, world, local_rank):
 
     kernels = profiled(B.JTRLAN_FP64)
     mixed["kernels_" + mixed["chosen"]] = profiled(forms[mixed["chosen"]][0])
+    if not args.no_mixed_16:
+        mixed["stencil_16x16x16x16"] = mixed_at_16(B, torch, stream, flush)
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     hbm_peak, hbm_src = measured_peaks()
     if "tflops" in kernels[dom]:
@@ -414,6 +451,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="stencil_8x8x8x8")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed-16", action="store_true", help="skip the 16^4 FP64 vs mixed comparison")
     ap.add_argument("--stencil-only", default=None, choices=sorted(STENCIL_LATTICES),
                     help="only time the FP32 stencil matvec on this lattice (for profiling)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)

@@ -92,6 +92,8 @@ struct Profiler {
 // Operator copy and Krylov basis in one working precision.
 struct Phase {
   OpDev op{};
+  OpDev opdf{};           // double-float phase, stencil: (hi, lo) links for the Lanczos products
+  bool dfmv = false;      // use opdf for the Lanczos products
   void* V = nullptr;      // n x (m + 1); float4 (hi, lo) pairs in a double-float phase
   void* Vtmp = nullptr;   // n x kk (rotation target; FP64 in a double-float phase)
   void* y = nullptr;      // the vector being built
@@ -292,6 +294,19 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
     c->pdf.df = true;
     JT_TRY(make_phase(c->pdf, sizeof(float4)));
     JT_TRY(c->dalloc(&c->pdf.x, (size_t)c->n * sizeof(double2)));
+    if (op->kind == JTRLAN_STENCIL4D) {   // (hi, lo) links for the compensated-FP32 matvec
+      OpDev& d = c->pdf.opdf;
+      d = o;
+      float4 *u = nullptr, *w = nullptr;
+      JT_TRY(c->dalloc(&u, (size_t)36 * o.vol * sizeof(float4)));
+      JT_TRY(c->dalloc(&w, (size_t)36 * o.vol * sizeof(float4)));
+      JT_CUDA(launch_links_df(o.U, u, o.vol, c->stream));
+      JT_CUDA(launch_links_df(o.W, w, o.vol, c->stream));
+      d.U = u; d.W = w;
+      c->pdf.dfmv = true;
+      const int nb = matvec_df_blocks(d);
+      if (nb > c->pdf.mv_nblk) JT_TRY(c->dalloc(&c->pdf.alpha_part, (size_t)nb * sizeof(double2)));
+    }
   }
   if (c->mixed) {  // the FP32 operator: links re-laid out structure-of-arrays, or FP32 dense blocks
     OpDev& q = c->p32.op;
@@ -402,14 +417,19 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
   for (int restart = 0; restart < max_restarts; ++restart) {
     // ---- Algorithm 2: m - k Lanczos steps, no host synchronisation inside
     if (ph.df) LAUNCH(K_OTHER, launch_fp64_from_df(col(ph.V, n, k, cs), ph.x, n, s));   // v_k in FP64
+    const int mv_parts = ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk;
     for (int j = k; j < m; ++j) {
-      const void* vj = ph.df ? ph.x : col(ph.V, n, j, cs);
-      LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)vj, (C*)ph.y, MV_ALPHA, ph.alpha_part,
-                                        nullptr, nullptr, 0, 0, nullptr, s));
+      if (ph.dfmv) {   // compensated FP32 on the (hi, lo) column and links, FP64 result
+        LAUNCH(K_MATVEC, launch_matvec_df(ph.opdf, col(ph.V, n, j, cs), ph.y, ph.alpha_part, s));
+      } else {
+        const void* vj = ph.df ? ph.x : col(ph.V, n, j, cs);
+        LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)vj, (C*)ph.y, MV_ALPHA, ph.alpha_part,
+                                          nullptr, nullptr, 0, 0, nullptr, s));
+      }
       a.j = j;
       if (ph.df) {
         // compensated FP32 reorthogonalisation of an FP64 vector against a (hi, lo) basis; see gsdf.cu
-        LAUNCH(K_GS_FIRST, launch_gsdf_first(a, ph.x, (const double2*)ph.alpha_part, ph.mv_nblk, s));
+        LAUNCH(K_GS_FIRST, launch_gsdf_first(a, ph.x, (const double2*)ph.alpha_part, mv_parts, s));
         LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
         LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
         for (int pass = 2; pass <= c->gs_passes; ++pass) {

@@ -364,6 +364,7 @@ __global__ void jsym_check_kernel(const cplx<R>* v, const cplx<R>* y, int64_t h,
 }  // namespace
 
 int gs_blocks(int64_t h, int* rows_per_block) {
+  // Row tiles of 32 row pairs, about four blocks per SM.
   const int64_t tiles = (h + 31) / 32;
   const int64_t target = 4 * 152;
   const int64_t tpb = (tiles + target - 1) / target;

@@ -81,6 +81,11 @@ cudaError_t launch_shrink_df(void* V, const void* Vsrc, int64_t n, const int* pe
 cudaError_t launch_gather_pairs_df(const void* V, int64_t n, const int* order, int nev, int partners, void* out,
                                    cudaStream_t s);
 cudaError_t launch_rotate_df(const void* V, int64_t n, int m, const double* Z, int kk, void* Vout, cudaStream_t s);
+// Stencil y (FP64) = A x with x and the links as (hi, lo) pairs; part (may be null) receives the
+// block partials of x^H y.  op.U / op.W: (hi, lo) links, structure-of-arrays [4][9][V].
+int matvec_df_blocks(const OpDev& op);
+cudaError_t launch_matvec_df(const OpDev& op, const void* x, void* y, double* part, cudaStream_t s);
+cudaError_t launch_links_df(const void* in, void* out, int64_t vol, cudaStream_t s);
 
 // Kernel classes for the optional per-kernel profile.
 enum KernelTag {
