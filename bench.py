@@ -439,7 +439,13 @@ def run_gb300(args, rank, world, local_rank):
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
     line["stencil_fp32"] = {k: stencil_apply_roofline(v) for k, v in STENCIL_LATTICES.items()}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, stats[-1]["n_matvec"] + stats[-1]["n_resid_matvec"])
+        # the oracle's own product count for the whole solve (it re-verifies locked pairs every
+        # restart, as Algorithm 1 is written), from the stored oracle run when there is one
+        g = os.path.join(GOLDEN, f"{args.workload}.json")
+        rec = json.load(open(g)).get("tol_1e-8", {}) if os.path.exists(g) else {}
+        full = (rec["n_matvec"] + rec["n_resid_matvec"]) if "n_resid_matvec" in rec else \
+            stats[-1]["n_matvec"] + stats[-1]["n_resid_matvec"]
+        line["cpu_baseline"] = cpu_baseline(args.workload, full)
     print(json.dumps(line), flush=True)
 
 
