@@ -211,6 +211,70 @@ jtrlan_status jtrlan_residual_norms_noalloc(const jtrlan_operator* op, const voi
                                             int ncols, const double* lambda, double* res,
                                             void* cuda_stream);
 
+/* ---- Batched dense solver: many independent dense operators of uneven order, one persistent launch.
+ *
+ * Algorithm 1 (TRLAN-JSYM) with the Lanczos step of Algorithm 2, as jtrlan_solve runs it on one
+ * operator, applied to `count` dense Hermitian J-symmetric operators at once: one kernel launch (held
+ * in a CUDA graph) in which each CTA takes instances, largest order first, from a device-side queue
+ * and runs the whole method for one instance with all control on the device.  Each instance starts
+ * from v_1 = (1, ..., 1)/sqrt(n) (Algorithm 1).  precision: JTRLAN_FP64 (plain FP64) or
+ * JTRLAN_MIXED_REORTH (products, Gram-Schmidt and rotation in compensated FP32 on (hi, lo) pairs;
+ * alpha/beta, the Ritz solve and the residuals in FP64).  */
+typedef struct jtrlan_batch jtrlan_batch;  /* opaque; owned by the library */
+
+typedef struct {
+  int count;               /* instances in the batch */
+  int n_ok;                /* instances that converged */
+  int64_t n_matvec;        /* Lanczos-step products A v_j, all instances */
+  int64_t n_resid_matvec;  /* products for true residuals, all instances */
+  int max_restarts;        /* largest outer-iteration count of any instance */
+  int grid;                /* CTAs of the persistent launch */
+  int threads;             /* threads per CTA */
+  int graph;               /* 1: the launch was replayed from a CUDA graph */
+  double solve_ms;         /* device time of the launch (CUDA events on the library's stream) */
+} jtrlan_batch_stats;
+
+/* Copies `count` dense operators (ops[i].kind == JTRLAN_DENSE, even ops[i].n with m < n/2, blocks
+ * host or device, complex128 or complex64, read during the call only) into one packed device array.
+ * params holds nev, m, mwin, tol, which, precision, max_restarts and gs_max_passes for every instance;
+ * v1 must be NULL and check_jsym 0.  Limits: m <= 64, nev <= 32.  The library runs the batch on a
+ * stream of its own, ordered after and before cuda_stream (NULL = legacy default) by events.
+ * Errors: JTRLAN_EINVAL (a limit or a field out of range, naming it), JTRLAN_ENOMEM, JTRLAN_ECUDA.
+ * *out is NULL on failure. */
+jtrlan_status jtrlan_batch_create(int count, const jtrlan_operator* ops, const jtrlan_params* params,
+                                  void* cuda_stream, jtrlan_batch** out);
+
+/* Fixes the launch shape: threads per CTA (a multiple of 32 in [64, 512]) and CTAs per SM
+ * (0 = as many as fit).  Errors: JTRLAN_EINVAL, JTRLAN_ECUDA. */
+jtrlan_status jtrlan_batch_set_shape(jtrlan_batch* b, int threads, int ctas_per_sm);
+
+/* Autotuner: solves the batch once per candidate launch shape (128, 256, 512 threads; 1 .. the
+ * occupancy limit of CTAs per SM), timing each with CUDA events, and keeps the fastest for later
+ * solves.  Any output pointer may be NULL.  Leaves the results of the last candidate in place.
+ * Errors: JTRLAN_EINVAL, JTRLAN_ECUDA. */
+jtrlan_status jtrlan_batch_tune(jtrlan_batch* b, int* threads, int* ctas_per_sm, double* best_ms);
+
+/* Solves every instance in one persistent launch (captured once into a CUDA graph per launch shape,
+ * replayed afterwards) and waits for it.  stats may be NULL.  Returns JTRLAN_OK if all instances
+ * converged, else the status of the first failing one (JTRLAN_ENOCONV, JTRLAN_EBREAKDOWN); the
+ * per-instance statuses are in jtrlan_batch_results.  Errors: JTRLAN_ECUDA. */
+jtrlan_status jtrlan_batch_solve(jtrlan_batch* b, jtrlan_batch_stats* stats);
+
+/* Host copies of the last solve, instance i at row i in creation order:
+ *   evals, res: count x nev doubles, sorted by eigenvalue toward the wanted end, res the true
+ *     residuals ||A x - lambda x|| (infinity where never tested);
+ *   istats: count x 4 ints {Lanczos products, outer iterations, status, residual products}.
+ * Any pointer may be NULL.  Errors: JTRLAN_ESTATE (no solve yet), JTRLAN_ECUDA. */
+jtrlan_status jtrlan_batch_results(jtrlan_batch* b, double* evals, double* res, int* istats);
+
+/* Eigenvectors of instance i (creation order) in the order of jtrlan_batch_results: column-major
+ * n_i x nev complex128 (double2) into evecs (host or device).  Errors: JTRLAN_EINVAL (index),
+ * JTRLAN_ESTATE (no solve, or instance i did not converge), JTRLAN_ECUDA. */
+jtrlan_status jtrlan_batch_vectors(jtrlan_batch* b, int i, void* evecs);
+
+/* Frees everything the batch owns (after synchronising its stream).  NULL is a no-op. */
+void jtrlan_batch_destroy(jtrlan_batch* b);
+
 /* Static text for a status code. */
 const char* jtrlan_status_string(jtrlan_status s);
 

@@ -21,7 +21,9 @@ JTRLAN_SMALLEST, JTRLAN_LARGEST = 0, 1
 JTRLAN_FP64, JTRLAN_MIXED, JTRLAN_MIXED_REORTH = 0, 1, 2
 
 EXPORTED = ["jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
-            "jtrlan_residual_norms_noalloc", "jtrlan_destroy", "jtrlan_status_string", "jtrlan_last_error"]
+            "jtrlan_residual_norms_noalloc", "jtrlan_destroy", "jtrlan_status_string", "jtrlan_last_error",
+            "jtrlan_batch_create", "jtrlan_batch_set_shape", "jtrlan_batch_tune", "jtrlan_batch_solve",
+            "jtrlan_batch_results", "jtrlan_batch_vectors", "jtrlan_batch_destroy"]
 NOALLOC_MAX_PARTIALS = 262144   # JTRLAN_NOALLOC_MAX_PARTIALS
 NOALLOC_MAX_COLS = 1024         # JTRLAN_NOALLOC_MAX_COLS
 
@@ -52,6 +54,15 @@ class jtrlan_stats(ctypes.Structure):
 
 
 MAX_KERNEL_CLASSES = 16
+
+
+class jtrlan_batch_stats(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("n_ok", ctypes.c_int), ("n_matvec", ctypes.c_int64),
+                ("n_resid_matvec", ctypes.c_int64), ("max_restarts", ctypes.c_int), ("grid", ctypes.c_int),
+                ("threads", ctypes.c_int), ("graph", ctypes.c_int), ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class jtrlan_profile(ctypes.Structure):
@@ -100,8 +111,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jtrlan_status_string.restype = ctypes.c_char_p
     lib.jtrlan_last_error.argtypes = []
     lib.jtrlan_last_error.restype = ctypes.c_char_p
+    lib.jtrlan_batch_create.argtypes = [ctypes.c_int, P(jtrlan_operator), P(jtrlan_params), ctypes.c_void_p,
+                                        P(ctypes.c_void_p)]
+    lib.jtrlan_batch_set_shape.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    lib.jtrlan_batch_tune.argtypes = [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double)]
+    lib.jtrlan_batch_solve.argtypes = [ctypes.c_void_p, P(jtrlan_batch_stats)]
+    lib.jtrlan_batch_results.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.jtrlan_batch_vectors.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    lib.jtrlan_batch_destroy.argtypes = [ctypes.c_void_p]
+    lib.jtrlan_batch_destroy.restype = None
     for f in ("jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
-              "jtrlan_residual_norms_noalloc"):
+              "jtrlan_residual_norms_noalloc", "jtrlan_batch_create", "jtrlan_batch_set_shape",
+              "jtrlan_batch_tune", "jtrlan_batch_solve", "jtrlan_batch_results", "jtrlan_batch_vectors"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -153,6 +174,49 @@ def jtrlan_residual_norms_noalloc(op: jtrlan_operator, x_ptr: int, ldx: int, nco
 def jtrlan_destroy(ctx):
     if ctx:
         load().jtrlan_destroy(ctx)
+
+
+def jtrlan_batch_create(ops, params: jtrlan_params, stream: int = 0) -> ctypes.c_void_p:
+    """ops: a sequence of jtrlan_operator (dense); copied into one contiguous array for the call."""
+    arr = (jtrlan_operator * len(ops))(*ops)
+    b = ctypes.c_void_p()
+    _check(load().jtrlan_batch_create(len(ops), arr, ctypes.byref(params), ctypes.c_void_p(stream),
+                                      ctypes.byref(b)))
+    return b
+
+
+def jtrlan_batch_set_shape(b, threads: int, ctas_per_sm: int):
+    _check(load().jtrlan_batch_set_shape(b, int(threads), int(ctas_per_sm)))
+
+
+def jtrlan_batch_tune(b) -> dict:
+    t, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(load().jtrlan_batch_tune(b, ctypes.byref(t), ctypes.byref(c), ctypes.byref(ms)))
+    return dict(threads=t.value, ctas_per_sm=c.value, best_ms=ms.value)
+
+
+def jtrlan_batch_solve(b, check: bool = True) -> dict:
+    """Returns the stats; with check=False a non-converged instance does not raise (status in 'status')."""
+    st = jtrlan_batch_stats()
+    status = load().jtrlan_batch_solve(b, ctypes.byref(st))
+    if check:
+        _check(status)
+    d = st.as_dict()
+    d["status"] = status
+    return d
+
+
+def jtrlan_batch_results(b, evals_ptr, res_ptr, istats_ptr):
+    _check(load().jtrlan_batch_results(b, evals_ptr, res_ptr, istats_ptr))
+
+
+def jtrlan_batch_vectors(b, i: int, evecs_ptr):
+    _check(load().jtrlan_batch_vectors(b, int(i), evecs_ptr))
+
+
+def jtrlan_batch_destroy(b):
+    if b:
+        load().jtrlan_batch_destroy(b)
 
 
 # ---------------------------------------------------------------- builders for the structs

@@ -141,6 +141,43 @@ cudaError_t launch_sum_columns(const void* X32, int64_t n, int ncol, void* out64
 cudaError_t launch_c128_to_c64(const void* in, void* out, int64_t count, cudaStream_t s);
 cudaError_t launch_links_soa(const void* in, void* out, int64_t vol, cudaStream_t s);
 
+// ------------------------------------------------------------------ batched dense solver (batch.cu)
+// Launch arguments of the persistent kernel: instance i has order n = 2 h[i]; its A11 and A12 are
+// h x h row-major at a_off[i] in the packed arrays (double2, or float4 (hi, lo) in the double-float
+// form).  Per CTA slot: V of nmax x (m + 1) 16-byte elements and an FP64 rotation target of
+// nmax x kk.  Results: out_ev / out_res [count][nev] sorted toward the wanted end, out_stats
+// [count][4] = {Lanczos products, outer iterations, status, residual products}, out_vec at
+// vec_off[i] (n x nev FP64 columns, written once converged).  queue: work counter, zero at launch.
+struct BatchArgs {
+  int count;
+  const int* order;
+  const int64_t* h;
+  const int64_t* a_off;
+  const void* A11;
+  const void* A12;
+  void* Vslots;
+  void* Tslots;
+  int64_t nmax;
+  int m, nev, mwin, kk, which, gs_passes, max_restarts;
+  double tol;
+  double* out_ev;
+  double* out_res;
+  int* out_stats;
+  void* out_vec;
+  const int64_t* vec_off;
+  int* queue;
+};
+constexpr int kBatchMaxM = 64;
+constexpr int kBatchMaxNev = 32;
+constexpr int kBatchMaxThreads = 512;
+size_t batch_smem_bytes(int64_t nmax, int m, int kk, int threads);
+cudaError_t batch_occupancy(bool df, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t launch_batch(bool df, const BatchArgs& a, int grid, int threads, cudaStream_t s);
+// In place: each double2 element becomes the float4 (hi.re, hi.im, lo.re, lo.im) with hi = fl32(x),
+// lo = fl32(x - hi).
+cudaError_t launch_split_df_inplace(void* A, int64_t count, cudaStream_t s);
+cudaError_t launch_c64_to_c128(const void* in, void* out, int64_t count, cudaStream_t s);
+
 // Sets the thread-local text returned by jtrlan_last_error().
 void set_last_error(const char* msg);
 

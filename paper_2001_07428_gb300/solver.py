@@ -91,3 +91,61 @@ class JTRLan:
             self.close()
         except Exception:
             pass
+
+
+class JTRLanBatch:
+    """Many dense operators (lists of A11, A12 blocks of uneven order) solved in one persistent launch.
+
+    ``precision`` is "fp64" or "mixed_reorth" (compensated FP32 products and Gram-Schmidt).
+    """
+
+    def __init__(self, A11s, A12s, *, nev, m, mwin, tol, which="smallest", max_restarts=0, gs_max_passes=0,
+                 precision="fp64", device="cuda"):
+        B.load()
+        self.device = torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device)
+        blocks = [(_dev(a, self.device), _dev(b, self.device)) for a, b in zip(A11s, A12s)]
+        ops = [B.dense_operator(2 * a.shape[0], a.data_ptr(), b.data_ptr()) for a, b in blocks]
+        self.ns = [int(o.n) for o in ops]
+        self.nev = int(nev)
+        w = B.JTRLAN_LARGEST if which == "largest" else B.JTRLAN_SMALLEST
+        prec = {"fp64": B.JTRLAN_FP64, "mixed_reorth": B.JTRLAN_MIXED_REORTH}[precision]
+        prm = B.params(nev, m, mwin, tol, which=w, precision=prec, max_restarts=max_restarts,
+                       gs_max_passes=gs_max_passes)
+        self.b = B.jtrlan_batch_create(ops, prm, self.stream.cuda_stream)
+        # jtrlan_batch_create copied the blocks and synchronised; they may be released now.
+
+    def tune(self) -> dict:
+        return B.jtrlan_batch_tune(self.b)
+
+    def set_shape(self, threads, ctas_per_sm=0):
+        B.jtrlan_batch_set_shape(self.b, threads, ctas_per_sm)
+
+    def solve(self, check=True) -> dict:
+        return B.jtrlan_batch_solve(self.b, check=check)
+
+    def results(self):
+        """(evals, res, istats): (count, nev), (count, nev), (count, 4) numpy arrays."""
+        cnt = len(self.ns)
+        ev = np.zeros((cnt, self.nev))
+        res = np.zeros((cnt, self.nev))
+        ist = np.zeros((cnt, 4), dtype=np.int32)
+        B.jtrlan_batch_results(self.b, ev.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p),
+                               ist.ctypes.data_as(ctypes.c_void_p))
+        return ev, res, ist
+
+    def vectors(self, i) -> torch.Tensor:
+        X = torch.empty((self.nev, self.ns[i]), dtype=torch.complex128, device=self.device)
+        B.jtrlan_batch_vectors(self.b, i, ctypes.c_void_p(X.data_ptr()))
+        return X.T   # n_i x nev
+
+    def close(self):
+        if getattr(self, "b", None):
+            B.jtrlan_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

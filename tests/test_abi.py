@@ -56,6 +56,9 @@ int main(void) {
          offsetof(jtrlan_stats, n_matvec_fp32));
   printf("%zu %zu %zu %zu\n", sizeof(jtrlan_profile), offsetof(jtrlan_profile, ms),
          offsetof(jtrlan_profile, launches), offsetof(jtrlan_profile, work));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_batch_stats), offsetof(jtrlan_batch_stats, n_matvec),
+         offsetof(jtrlan_batch_stats, max_restarts), offsetof(jtrlan_batch_stats, graph),
+         offsetof(jtrlan_batch_stats, solve_ms));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -67,6 +70,9 @@ int main(void) {
     assert got[2] == [ctypes.sizeof(S), S.n_restarts.offset, S.solve_ms.offset, S.n_launches.offset,
                       S.n_ritz_fallbacks.offset, S.n_matvec_fp32.offset]
     assert got[3] == [ctypes.sizeof(F), F.ms.offset, F.launches.offset, F.work.offset]
+    Q = B.jtrlan_batch_stats
+    assert got[4] == [ctypes.sizeof(Q), Q.n_matvec.offset, Q.max_restarts.offset, Q.graph.offset,
+                      Q.solve_ms.offset]
 
 
 def test_status_strings(lib):
@@ -116,3 +122,51 @@ def test_null_context_calls(lib):
     assert lib.jtrlan_apply(None, None, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_get_profile(None, None) == B.JTRLAN_EINVAL
     lib.jtrlan_destroy(None)
+
+
+@pytest.mark.parametrize("case", ["count", "stencil", "odd_n", "m_ge_half", "big_m", "big_nev", "mixed", "v1",
+                                  "check_jsym", "which", "tol"])
+def test_batch_invalid_arguments_rejected_without_gpu(lib, case):
+    ops = [B.dense_operator(n, DUMMY, DUMMY) for n in (64, 100, 128)]
+    prm = B.params(8, 24, 12, 1e-8)
+    if case == "count":
+        ops = []
+    elif case == "stencil":
+        ops[1] = B.stencil_operator((4, 4, 4, 4), 8.5, 0.3, DUMMY, DUMMY)
+    elif case == "odd_n":
+        ops[2].n = 129
+    elif case == "m_ge_half":
+        ops[0].n = 48
+    elif case == "big_m":
+        ops = [B.dense_operator(400, DUMMY, DUMMY)]
+        prm.m = 65
+    elif case == "big_nev":
+        ops = [B.dense_operator(400, DUMMY, DUMMY)]
+        prm.m, prm.nev = 60, 33
+    elif case == "mixed":
+        prm.precision = B.JTRLAN_MIXED
+    elif case == "v1":
+        prm.v1 = DUMMY
+    elif case == "check_jsym":
+        prm.check_jsym = 1
+    elif case == "which":
+        prm.which = 3
+    elif case == "tol":
+        prm.tol = -1.0
+    if case == "count":
+        b = ctypes.c_void_p()
+        st = lib.jtrlan_batch_create(0, None, ctypes.byref(prm), None, ctypes.byref(b))
+        assert st == B.JTRLAN_EINVAL and not b.value
+        return
+    with pytest.raises(B.JTRLanError) as ei:
+        B.jtrlan_batch_create(ops, prm, 0)
+    assert ei.value.status == B.JTRLAN_EINVAL
+
+
+def test_batch_null_calls(lib):
+    assert lib.jtrlan_batch_solve(None, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_batch_results(None, None, None, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_batch_vectors(None, 0, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_batch_tune(None, None, None, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_batch_set_shape(None, 256, 0) == B.JTRLAN_EINVAL
+    lib.jtrlan_batch_destroy(None)
