@@ -230,6 +230,122 @@ def stencil_apply_roofline(dims, reps=20, seed=4):
             "frac_of_hbm": round(gbs / hbm, 4), "hbm_peak_gbs": hbm, "peak_source": src}
 
 
+# ---------------------------------------------------------------- batched dense instances
+BATCH = dict(count=512, lo=64, hi=512, size_seed=2, seed0=1000, nev=8, m=24, mwin=12)
+
+
+def batch_instances():
+    """512 dense Hermitian J-symmetric instances (A11 = (G+G^H)/2, A12 = (K-K^T)/2, complex Gaussian),
+    n uniform over the even numbers 64..512, seeded as the parity test seeds them."""
+    sizes = inputs.batched_dense_sizes(BATCH["count"], BATCH["lo"], BATCH["hi"], seed=BATCH["size_seed"])
+    return sizes, [inputs.dense_jsym(int(n) // 2, BATCH["seed0"] + i) for i, n in enumerate(sizes)]
+
+
+def batched_oracle_sample(picks):
+    """Oracle (CPU FP64) time for the instances `picks` of the batch; run as a subprocess."""
+    from oracle import jsym
+    from oracle import trlan_jsym as tj
+    sizes, blocks = batch_instances()
+    t0 = time.perf_counter()
+    for i in picks:
+        A11, A12 = blocks[i]
+        tj.trlan_jsym(lambda x: jsym.dense_matvec(A11, A12, x), int(sizes[i]), BATCH["nev"], BATCH["m"],
+                      BATCH["mwin"], TOL)
+    return time.perf_counter() - t0
+
+
+def batched_dense(B, torch, stream, steps, warmup, cpu=True):
+    """The batch in one persistent launch per solve (CUDA-graph replay, autotuned launch shape), plain
+    FP64 and the compensated-FP32 form; K timed solves each after W warm-up solves.  Inputs (408 MB of
+    packed blocks) exceed L2.  Roofline: algorithmic matvec work (32 flop and 32 bytes per (row pair,
+    column) of the packed blocks per product) over the solve time."""
+    import ctypes
+    sizes, blocks = batch_instances()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    h2 = (sizes // 2).astype(np.int64) ** 2
+    out = {"workload": "dense_batch_512_n64-512", "count": BATCH["count"], "n_range": [BATCH["lo"], BATCH["hi"]],
+           "nev": BATCH["nev"], "m": BATCH["m"], "mwin": BATCH["mwin"], "tol": TOL,
+           "packed_bytes": int(2 * 16 * h2.sum())}
+    Ad = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in blocks]
+    ops = [B.dense_operator(2 * a.shape[0], a.data_ptr(), b.data_ptr()) for a, b in Ad]
+    evs = {}
+    hbm, hsrc = measured_peaks()
+    for name, prec in (("fp64", B.JTRLAN_FP64), ("mixed_reorth", B.JTRLAN_MIXED_REORTH)):
+        bt = B.jtrlan_batch_create(ops, B.params(BATCH["nev"], BATCH["m"], BATCH["mwin"], TOL, precision=prec),
+                                   stream.cuda_stream)
+        tuned = B.jtrlan_batch_tune(bt)
+        for _ in range(warmup):
+            st = B.jtrlan_batch_solve(bt)
+        ts = []
+        for _ in range(steps):
+            st = B.jtrlan_batch_solve(bt)
+            ts.append(st["solve_ms"] * 1e-3)
+        ev = np.zeros((BATCH["count"], BATCH["nev"]))
+        res = np.zeros_like(ev)
+        ist = np.zeros((BATCH["count"], B.BATCH_STATS), dtype=np.int32)
+        B.jtrlan_batch_results(bt, ev.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p),
+                               ist.ctypes.data_as(ctypes.c_void_p))
+        B.jtrlan_batch_destroy(bt)
+        # one more solve with per-phase cycle counters (thread 0 of each CTA reads clock64 at barriers)
+        bp = B.jtrlan_batch_create(ops, B.params(BATCH["nev"], BATCH["m"], BATCH["mwin"], TOL, precision=prec,
+                                                 profile=1), stream.cuda_stream)
+        B.jtrlan_batch_set_shape(bp, tuned["threads"], tuned["ctas_per_sm"])
+        sp = B.jtrlan_batch_solve(bp)
+        B.jtrlan_batch_destroy(bp)
+        evs[name] = ev
+        t = statistics.mean(ts)
+        prods = (ist[:, 0] + ist[:, 3]).astype(np.int64)
+        flop = float(32 * (prods * h2).sum())
+        byts = float(2 * 16 * (prods * h2).sum())
+        e = {"value": t, "unit": "s", "instances_per_s": round(BATCH["count"] / t, 1), "n_ok": int(st["n_ok"]),
+             "n_matvec": int(st["n_matvec"]), "n_resid_matvec": int(st["n_resid_matvec"]),
+             "max_outer_iterations": int(st["max_restarts"]), "max_residual": float(res.max()),
+             "grid": st["grid"], "threads": st["threads"], "tuned": tuned, "graph": st["graph"],
+             "n_gs_passes": int(st["n_gs_passes"]), "n_ritz_fallbacks": int(st["n_ritz_fallbacks"]),
+             "phase_share": {k: round(v, 4) for k, v in sp["phase_frac"].items()},
+             "matvec_tflops": round(flop / t / 1e12, 4), "matvec_gbs": round(byts / t / 1e9, 1)}
+        e["frac_of_fp64_peak"] = round(e["matvec_tflops"] / FP64_PEAK_TFLOPS, 4)
+        e["frac_of_hbm"] = round(e["matvec_gbs"] / hbm, 4)
+        out[name] = e
+    out["speedup_vs_fp64"] = round(out["fp64"]["value"] / out["mixed_reorth"]["value"], 3)
+    out["max_rel_eig_diff_vs_fp64"] = float(np.max(np.abs(evs["mixed_reorth"] - evs["fp64"]) / np.abs(evs["fp64"])))
+    out["hbm_peak_gbs"], out["hbm_peak_source"] = hbm, hsrc
+    # end to end: pinned host blocks -> create (H2D) -> solve -> eigenvalues and vectors to host
+    Hh = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in blocks]
+    ops_h = [B.dense_operator(2 * a.shape[0], a.data_ptr(), b.data_ptr()) for a, b in Hh]
+    Xh = torch.empty(int(sizes.sum()) * BATCH["nev"], dtype=torch.complex128).pin_memory()
+    ev = np.zeros((BATCH["count"], BATCH["nev"]))
+    chosen = min(("fp64", "mixed_reorth"), key=lambda k: out[k]["value"])
+    prec = B.JTRLAN_FP64 if chosen == "fp64" else B.JTRLAN_MIXED_REORTH
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt = B.jtrlan_batch_create(ops_h, B.params(BATCH["nev"], BATCH["m"], BATCH["mwin"], TOL, precision=prec),
+                               stream.cuda_stream)
+    B.jtrlan_batch_set_shape(bt, out[chosen]["tuned"]["threads"], out[chosen]["tuned"]["ctas_per_sm"])
+    B.jtrlan_batch_solve(bt)
+    B.jtrlan_batch_results(bt, ev.ctypes.data_as(ctypes.c_void_p), None, None)
+    off = 0
+    for i, n in enumerate(sizes):
+        B.jtrlan_batch_vectors(bt, i, ctypes.c_void_p(Xh.data_ptr() + 16 * off))
+        off += int(n) * BATCH["nev"]
+    B.jtrlan_batch_destroy(bt)
+    te = time.perf_counter() - t0
+    out["e2e"] = {"form": chosen, "value": te, "unit": "s", "h2d_bytes": out["packed_bytes"],
+                  "d2h_bytes": int(Xh.numel() * 16 + ev.size * 8)}
+    if cpu:
+        order = np.argsort(sizes)
+        picks = [int(order[j]) for j in range(0, BATCH["count"], 16)]   # 32 instances across the sizes
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--batched-oracle-sample",
+                            ",".join(map(str, picks))], capture_output=True, text=True, timeout=1800,
+                           env=dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1"))
+        sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+        scale = float(h2.sum() / h2[picks].sum())
+        out["cpu_baseline"] = {"value": sec * scale, "unit": "s", "cores": 1, "kind": "oracle",
+                               "sample": f"32 of the 512 instances (every 16th by size), {sec:.1f} s, scaled by "
+                                         f"sum(h^2) over all / over the sample = {scale:.1f}"}
+    return out
+
+
 # ---------------------------------------------------------------- the reference arm (the oracle)
 def run_reference(args, rank, world):
     if rank != 0:
@@ -438,6 +554,9 @@ def run_gb300(args, rank, world, local_rank):
             "kernels": kernels,
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
     line["stencil_fp32"] = {k: stencil_apply_roofline(v) for k, v in STENCIL_LATTICES.items()}
+    if not args.no_batched:
+        line["batched_dense"] = batched_dense(B, torch, stream, args.steps, args.warmup,
+                                              cpu=world == 1 and not args.no_cpu_baseline)
     if world == 1 and not args.no_cpu_baseline:
         # the oracle's own product count for the whole solve (it re-verifies locked pairs every
         # restart, as Algorithm 1 is written), from the stored oracle run when there is one
@@ -460,9 +579,15 @@ def main():
     ap.add_argument("--no-mixed-16", action="store_true", help="skip the 16^4 FP64 vs mixed comparison")
     ap.add_argument("--stencil-only", default=None, choices=sorted(STENCIL_LATTICES),
                     help="only time the FP32 stencil matvec on this lattice (for profiling)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched dense instances")
+    ap.add_argument("--batched-only", action="store_true", help="only time the batched dense instances")
+    ap.add_argument("--batched-oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-restarts", type=int, default=4, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.batched_oracle_sample:
+        print(json.dumps({"seconds": batched_oracle_sample([int(i) for i in args.batched_oracle_sample.split(",")])}))
+        return
     if args.oracle_sample:
         sec, done = oracle_sample(args.oracle_sample, args.sample_restarts)
         print(json.dumps({"seconds": sec, "products": done}))
@@ -475,6 +600,13 @@ def main():
         return
     if args.stencil_only:
         print(json.dumps(stencil_apply_roofline(STENCIL_LATTICES[args.stencil_only])), flush=True)
+        return
+    if args.batched_only:
+        import torch
+        from paper_2001_07428_gb300 import binding as B
+        B.load()
+        print(json.dumps(batched_dense(B, torch, torch.cuda.current_stream(), args.steps, args.warmup,
+                                       cpu=not args.no_cpu_baseline)), flush=True)
         return
     if world > 1:
         import torch

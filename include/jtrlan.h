@@ -232,12 +232,16 @@ typedef struct {
   int threads;             /* threads per CTA */
   int graph;               /* 1: the launch was replayed from a CUDA graph */
   double solve_ms;         /* device time of the launch (CUDA events on the library's stream) */
+  int64_t n_ritz_fallbacks;  /* restarts whose fast Ritz solve failed a check (Jacobi used) */
+  int64_t n_gs_passes;       /* Gram-Schmidt passes, all instances */
+  double phase_frac[5];      /* params.profile only: share of CTA cycles in the Lanczos product,
+                                Gram-Schmidt, Ritz solve, rotation + shrink, residual checks */
 } jtrlan_batch_stats;
 
 /* Copies `count` dense operators (ops[i].kind == JTRLAN_DENSE, even ops[i].n with m < n/2, blocks
  * host or device, complex128 or complex64, read during the call only) into one packed device array.
- * params holds nev, m, mwin, tol, which, precision, max_restarts and gs_max_passes for every instance;
- * v1 must be NULL and check_jsym 0.  Limits: m <= 64, nev <= 32.  The library runs the batch on a
+ * params holds nev, m, mwin, tol, which, precision, max_restarts, gs_max_passes and profile (per-phase
+ * cycle counts, reported in jtrlan_batch_stats) for every instance; v1 must be NULL and check_jsym 0.  Limits: m <= 64, nev <= 32.  The library runs the batch on a
  * stream of its own, ordered after and before cuda_stream (NULL = legacy default) by events.
  * Errors: JTRLAN_EINVAL (a limit or a field out of range, naming it), JTRLAN_ENOMEM, JTRLAN_ECUDA.
  * *out is NULL on failure. */
@@ -263,8 +267,10 @@ jtrlan_status jtrlan_batch_solve(jtrlan_batch* b, jtrlan_batch_stats* stats);
 /* Host copies of the last solve, instance i at row i in creation order:
  *   evals, res: count x nev doubles, sorted by eigenvalue toward the wanted end, res the true
  *     residuals ||A x - lambda x|| (infinity where never tested);
- *   istats: count x 4 ints {Lanczos products, outer iterations, status, residual products}.
+ *   istats: count x JTRLAN_BATCH_STATS ints {Lanczos products, outer iterations, status, residual
+ *     products, Ritz fallbacks, Gram-Schmidt passes}.
  * Any pointer may be NULL.  Errors: JTRLAN_ESTATE (no solve yet), JTRLAN_ECUDA. */
+#define JTRLAN_BATCH_STATS 6
 jtrlan_status jtrlan_batch_results(jtrlan_batch* b, double* evals, double* res, int* istats);
 
 /* Eigenvectors of instance i (creation order) in the order of jtrlan_batch_results: column-major

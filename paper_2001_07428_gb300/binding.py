@@ -59,10 +59,18 @@ MAX_KERNEL_CLASSES = 16
 class jtrlan_batch_stats(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int), ("n_ok", ctypes.c_int), ("n_matvec", ctypes.c_int64),
                 ("n_resid_matvec", ctypes.c_int64), ("max_restarts", ctypes.c_int), ("grid", ctypes.c_int),
-                ("threads", ctypes.c_int), ("graph", ctypes.c_int), ("solve_ms", ctypes.c_double)]
+                ("threads", ctypes.c_int), ("graph", ctypes.c_int), ("solve_ms", ctypes.c_double),
+                ("n_ritz_fallbacks", ctypes.c_int64), ("n_gs_passes", ctypes.c_int64),
+                ("phase_frac", ctypes.c_double * 5)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["phase_frac"] = dict(zip(BATCH_PHASES, self.phase_frac))
+        return d
+
+
+BATCH_STATS = 6   # JTRLAN_BATCH_STATS
+BATCH_PHASES = ("lanczos_product", "gram_schmidt", "ritz", "rotate_shrink", "residuals")
 
 
 class jtrlan_profile(ctypes.Structure):

@@ -56,6 +56,7 @@ struct jtrlan_batch {
   double* out_ev = nullptr;
   double* out_res = nullptr;
   int* out_stats = nullptr;
+  long long* prof = nullptr;    // per-instance phase cycles (params.profile)
   void* out_vec = nullptr;
   int* queue = nullptr;
   int n_sm = 0;
@@ -180,8 +181,12 @@ jtrlan_status create_batch(int count, const jtrlan_operator* ops, const jtrlan_p
   b->out_ev = (double*)vp;
   JB_TRY(b->dalloc(&vp, (size_t)count * p->nev * sizeof(double)));
   b->out_res = (double*)vp;
-  JB_TRY(b->dalloc(&vp, (size_t)count * 4 * sizeof(int)));
+  JB_TRY(b->dalloc(&vp, (size_t)count * kBatchStats * sizeof(int)));
   b->out_stats = (int*)vp;
+  if (p->profile) {
+    JB_TRY(b->dalloc(&vp, (size_t)count * kBatchPhases * sizeof(long long)));
+    b->prof = (long long*)vp;
+  }
   JB_TRY(b->dalloc(&b->out_vec, (size_t)v_total * sizeof(double2)));
   JB_TRY(b->dalloc(&vp, sizeof(int)));
   b->queue = (int*)vp;
@@ -257,6 +262,7 @@ BatchArgs args_of(const jtrlan_batch* b) {
   a.out_stats = b->out_stats;
   a.out_vec = b->out_vec;
   a.vec_off = b->d_voff;
+  a.prof = b->prof;
   a.queue = b->queue;
   return a;
 }
@@ -367,17 +373,31 @@ jtrlan_status jtrlan_batch_solve(jtrlan_batch* b, jtrlan_batch_stats* stats) {
   float ms = 0.f;
   JB_TRY(run_once(b, b->threads, b->ctas_per_sm, true, &ms));
   b->solved = true;
-  std::vector<int> st((size_t)b->count * 4);
+  std::vector<int> st((size_t)b->count * kBatchStats);
   JB_CUDA(cudaMemcpy(st.data(), b->out_stats, st.size() * sizeof(int), cudaMemcpyDeviceToHost));
   int n_ok = 0, max_rs = 0;
-  int64_t mv = 0, rmv = 0;
+  int64_t mv = 0, rmv = 0, fb = 0, gs = 0;
   jtrlan_status worst = JTRLAN_OK;
   for (int i = 0; i < b->count; ++i) {
-    mv += st[4 * i];
-    max_rs = std::max(max_rs, st[4 * i + 1]);
-    rmv += st[4 * i + 3];
-    if (st[4 * i + 2] == JTRLAN_OK) ++n_ok;
-    else if (worst == JTRLAN_OK) worst = (jtrlan_status)st[4 * i + 2];
+    const int* o = &st[(size_t)kBatchStats * i];
+    mv += o[0];
+    max_rs = std::max(max_rs, o[1]);
+    rmv += o[3];
+    fb += o[4];
+    gs += o[5];
+    if (o[2] == JTRLAN_OK) ++n_ok;
+    else if (worst == JTRLAN_OK) worst = (jtrlan_status)o[2];
+  }
+  double phase[kBatchPhases] = {};
+  if (b->prof) {
+    std::vector<long long> pr((size_t)b->count * kBatchPhases);
+    JB_CUDA(cudaMemcpy(pr.data(), b->prof, pr.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+    double tot = 0.0;
+    for (size_t q = 0; q < pr.size(); ++q) {
+      phase[q % kBatchPhases] += (double)pr[q];
+      tot += (double)pr[q];
+    }
+    for (int q = 0; q < kBatchPhases; ++q) phase[q] = tot > 0 ? phase[q] / tot : 0.0;
   }
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -390,6 +410,9 @@ jtrlan_status jtrlan_batch_solve(jtrlan_batch* b, jtrlan_batch_stats* stats) {
     stats->grid = b->exec_grid;
     stats->threads = b->exec_threads;
     stats->graph = 1;
+    stats->n_ritz_fallbacks = fb;
+    stats->n_gs_passes = gs;
+    for (int q = 0; q < kBatchPhases; ++q) stats->phase_frac[q] = phase[q];
   }
   if (worst != JTRLAN_OK) return bfail(worst, "at least one instance did not converge (see per-instance status)");
   return JTRLAN_OK;
@@ -401,7 +424,8 @@ jtrlan_status jtrlan_batch_results(jtrlan_batch* b, double* evals, double* res, 
   const size_t ne = (size_t)b->count * b->nev;
   if (evals) JB_CUDA(cudaMemcpy(evals, b->out_ev, ne * sizeof(double), cudaMemcpyDeviceToHost));
   if (res) JB_CUDA(cudaMemcpy(res, b->out_res, ne * sizeof(double), cudaMemcpyDeviceToHost));
-  if (istats) JB_CUDA(cudaMemcpy(istats, b->out_stats, (size_t)b->count * 4 * sizeof(int), cudaMemcpyDeviceToHost));
+  if (istats)
+    JB_CUDA(cudaMemcpy(istats, b->out_stats, (size_t)b->count * kBatchStats * sizeof(int), cudaMemcpyDeviceToHost));
   return JTRLAN_OK;
 }
 
@@ -409,8 +433,8 @@ jtrlan_status jtrlan_batch_vectors(jtrlan_batch* b, int i, void* evecs) {
   if (!b || !evecs) return bfail(JTRLAN_EINVAL, "null argument");
   if (i < 0 || i >= b->count) return bfail(JTRLAN_EINVAL, "instance index out of range");
   if (!b->solved) return bfail(JTRLAN_ESTATE, "no solve to report");
-  int st[4];
-  JB_CUDA(cudaMemcpy(st, b->out_stats + 4 * i, sizeof(st), cudaMemcpyDeviceToHost));
+  int st[kBatchStats];
+  JB_CUDA(cudaMemcpy(st, b->out_stats + (size_t)kBatchStats * i, sizeof(st), cudaMemcpyDeviceToHost));
   if (st[2] != JTRLAN_OK) return bfail(JTRLAN_ESTATE, "instance did not converge");
   const size_t bytes = (size_t)(2 * b->h[i]) * b->nev * sizeof(double2);
   JB_CUDA(cudaMemcpy(evecs, (double2*)b->out_vec + b->vec_off[i], bytes, cudaMemcpyDefault));

@@ -146,8 +146,9 @@ cudaError_t launch_links_soa(const void* in, void* out, int64_t vol, cudaStream_
 // h x h row-major at a_off[i] in the packed arrays (double2, or float4 (hi, lo) in the double-float
 // form).  Per CTA slot: V of nmax x (m + 1) 16-byte elements and an FP64 rotation target of
 // nmax x kk.  Results: out_ev / out_res [count][nev] sorted toward the wanted end, out_stats
-// [count][4] = {Lanczos products, outer iterations, status, residual products}, out_vec at
-// vec_off[i] (n x nev FP64 columns, written once converged).  queue: work counter, zero at launch.
+// [count][kBatchStats] = {Lanczos products, outer iterations, status, residual products, Ritz
+// fallbacks, Gram-Schmidt passes}, out_vec at vec_off[i] (n x nev FP64 columns, written once
+// converged), prof (optional) [count][kBatchPhases] SM cycles per phase.  queue: work counter.
 struct BatchArgs {
   int count;
   const int* order;
@@ -165,8 +166,11 @@ struct BatchArgs {
   int* out_stats;
   void* out_vec;
   const int64_t* vec_off;
+  long long* prof;
   int* queue;
 };
+constexpr int kBatchStats = 6;
+constexpr int kBatchPhases = 5;   // Lanczos product + alpha, Gram-Schmidt, Ritz, rotation + shrink, residuals
 constexpr int kBatchMaxM = 64;
 constexpr int kBatchMaxNev = 32;
 constexpr int kBatchMaxThreads = 512;

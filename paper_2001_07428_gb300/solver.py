@@ -100,7 +100,7 @@ class JTRLanBatch:
     """
 
     def __init__(self, A11s, A12s, *, nev, m, mwin, tol, which="smallest", max_restarts=0, gs_max_passes=0,
-                 precision="fp64", device="cuda"):
+                 precision="fp64", profile=False, device="cuda"):
         B.load()
         self.device = torch.device(device)
         self.stream = torch.cuda.current_stream(self.device)
@@ -111,7 +111,7 @@ class JTRLanBatch:
         w = B.JTRLAN_LARGEST if which == "largest" else B.JTRLAN_SMALLEST
         prec = {"fp64": B.JTRLAN_FP64, "mixed_reorth": B.JTRLAN_MIXED_REORTH}[precision]
         prm = B.params(nev, m, mwin, tol, which=w, precision=prec, max_restarts=max_restarts,
-                       gs_max_passes=gs_max_passes)
+                       gs_max_passes=gs_max_passes, profile=int(profile))
         self.b = B.jtrlan_batch_create(ops, prm, self.stream.cuda_stream)
         # jtrlan_batch_create copied the blocks and synchronised; they may be released now.
 
@@ -125,11 +125,12 @@ class JTRLanBatch:
         return B.jtrlan_batch_solve(self.b, check=check)
 
     def results(self):
-        """(evals, res, istats): (count, nev), (count, nev), (count, 4) numpy arrays."""
+        """(evals, res, istats): (count, nev), (count, nev), (count, 6) numpy arrays; istats columns:
+        Lanczos products, outer iterations, status, residual products, Ritz fallbacks, GS passes."""
         cnt = len(self.ns)
         ev = np.zeros((cnt, self.nev))
         res = np.zeros((cnt, self.nev))
-        ist = np.zeros((cnt, 4), dtype=np.int32)
+        ist = np.zeros((cnt, B.BATCH_STATS), dtype=np.int32)
         B.jtrlan_batch_results(self.b, ev.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p),
                                ist.ctypes.data_as(ctypes.c_void_p))
         return ev, res, ist

@@ -56,9 +56,9 @@ int main(void) {
          offsetof(jtrlan_stats, n_matvec_fp32));
   printf("%zu %zu %zu %zu\n", sizeof(jtrlan_profile), offsetof(jtrlan_profile, ms),
          offsetof(jtrlan_profile, launches), offsetof(jtrlan_profile, work));
-  printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_batch_stats), offsetof(jtrlan_batch_stats, n_matvec),
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_batch_stats), offsetof(jtrlan_batch_stats, n_matvec),
          offsetof(jtrlan_batch_stats, max_restarts), offsetof(jtrlan_batch_stats, graph),
-         offsetof(jtrlan_batch_stats, solve_ms));
+         offsetof(jtrlan_batch_stats, solve_ms), offsetof(jtrlan_batch_stats, phase_frac));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -72,7 +72,7 @@ int main(void) {
     assert got[3] == [ctypes.sizeof(F), F.ms.offset, F.launches.offset, F.work.offset]
     Q = B.jtrlan_batch_stats
     assert got[4] == [ctypes.sizeof(Q), Q.n_matvec.offset, Q.max_restarts.offset, Q.graph.offset,
-                      Q.solve_ms.offset]
+                      Q.solve_ms.offset, Q.phase_frac.offset]
 
 
 def test_status_strings(lib):
