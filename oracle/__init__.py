@@ -11,4 +11,8 @@ Contents:
                  brute-force dense assembly for small problems.
   trlan_jsym  -- Algorithm 1 (TRLAN-JSYM) and Algorithm 2 (LANCZOS_JSYM) in FP64,
                  in the paper's order and notation.
+  filter      -- polynomial filters p(A) (Chebyshev recurrence, damped step coefficients);
+                 the paper has none, these are standard definitions.
+  mlp         -- the 3-layer perceptron that predicts filter coefficients: forward pass,
+                 gradient and one Adam step in FP64.
 """
