@@ -99,7 +99,15 @@ typedef struct {
  *     on a fixed pseudo-random v and fails with JTRLAN_ENOTJSYM otherwise.
  *   profile: if nonzero, jtrlan_solve brackets every kernel launch with CUDA events on the context
  *     stream and sums the device time per kernel class (read with jtrlan_get_profile).  This adds
- *     two event records per launch; leave it off for timed runs. */
+ *     two event records per launch; leave it off for timed runs.
+ *   filter_degree, filter_coeffs, filter_lo, filter_hi (the paper has no filter): with d =
+ *     filter_degree > 0 the FP32 phase of JTRLAN_MIXED runs Algorithm 1 on B = p(A) =
+ *     sum_k g_k T_k((A - c I)/e), c = (lo + hi)/2, e = (hi - lo)/2, T_k the Chebyshev polynomials,
+ *     wanting the LARGEST eigenvalues of B; real g_k keep B Hermitian J-symmetric.  That phase is
+ *     judged by the Lanczos residual estimates |t_{m+1,i}| of B only (to 1e-5 max|t|); the second,
+ *     unfiltered phase then starts from the sum of its Ritz vectors and certifies every pair with
+ *     the true residual of A, so a poor filter costs time, never accuracy.  [lo, hi] should contain
+ *     the spectrum (jtrlan_bounds estimates it); 1 <= d <= 1024. */
 typedef struct {
   int nev;
   int m;
@@ -112,6 +120,9 @@ typedef struct {
   const void* v1;
   int check_jsym;
   int profile;        /* nonzero: time every kernel launch with CUDA events (jtrlan_get_profile) */
+  int filter_degree;  /* 0: none; else the degree d of the polynomial filter (JTRLAN_MIXED only) */
+  const double* filter_coeffs;  /* host, d + 1 Chebyshev coefficients g_0..g_d (copied at create) */
+  double filter_lo, filter_hi;  /* the window [a, b] of the Chebyshev variable (A - c)/e */
 } jtrlan_params;
 
 /* Counters of the last solve (Sec. 3 counts only the Lanczos-step products as N_MV). */
@@ -181,6 +192,26 @@ jtrlan_status jtrlan_get_profile(jtrlan_ctx* ctx, jtrlan_profile* out);
 
 /* Frees everything the context owns (after synchronising its stream).  NULL is a no-op. */
 void jtrlan_destroy(jtrlan_ctx* ctx);
+
+/* y = p(A) x with the filter of params (filter_degree > 0) and the FP32 operator of a JTRLAN_MIXED
+ * context: x, y DEVICE complex64 vectors of n entries (distinct).  Enqueued on the context stream.
+ * Errors: JTRLAN_EINVAL (null, or no filter), JTRLAN_ECUDA. */
+jtrlan_status jtrlan_apply_filter(jtrlan_ctx* ctx, const void* x, void* y);
+
+/* Spectral bounds for a filter window (the paper has no counterpart): `steps` Lanczos steps of
+ * Algorithm 2 on A (full reorthogonalisation, no restart) from a fixed pseudo-random start, in the
+ * context's working precision (FP32 for JTRLAN_MIXED), then the Rayleigh-Ritz values of the
+ * steps x steps tridiagonal in FP64.  *lo = the smallest Ritz value (an upper bound of lambda_min),
+ * *hi = the largest Ritz value + beta_steps (an estimate, not a guarantee, of an upper bound of
+ * lambda_max).  2 <= steps <= m.  Synchronises the context stream.  Errors: JTRLAN_EINVAL,
+ * JTRLAN_EBREAKDOWN, JTRLAN_ECUDA. */
+jtrlan_status jtrlan_bounds(jtrlan_ctx* ctx, int steps, double* lo, double* hi);
+
+/* Jackson-damped Chebyshev coefficients of the step [x <= tau_i] (Jackson damping as in Weisse et
+ * al., Rev. Mod. Phys. 78, 275 (2006), N = degree + 1 moments), the targets of the learned filter:
+ * tau: device, count doubles; out: device, count x (degree + 1) floats.  Enqueued on cuda_stream.
+ * Errors: JTRLAN_EINVAL, JTRLAN_ECUDA. */
+jtrlan_status jtrlan_damped_step(const double* tau, int count, int degree, float* out, void* cuda_stream);
 
 /* Residual norms without device allocation.
  *
@@ -280,6 +311,45 @@ jtrlan_status jtrlan_batch_vectors(jtrlan_batch* b, int i, void* evecs);
 
 /* Frees everything the batch owns (after synchronising its stream).  NULL is a no-op. */
 void jtrlan_batch_destroy(jtrlan_batch* b);
+
+/* ---- The learned filter's network (the paper has none): a 3-layer perceptron in FP32,
+ *   A1 = tanh(X W1^T + b1), A2 = tanh(A1 W2^T + b2), Y = A2 W3^T + b3,
+ * trained on the mean squared error L = mean((Y - T)^2) with Adam (Kingma and Ba, ICLR 2015;
+ * b1 = 0.9, b2 = 0.999, eps = 1e-8), all in the library's CUDA kernels.  Parameters are one packed
+ * FP32 vector: W1 (width x n_in, row-major), b1, W2 (width x width), b2, W3 (n_out x width), b3, of
+ * jtrlan_mlp_param_count(n_in, width, n_out) floats.  Batches X (N x n_in) and T, Y (N x n_out) are
+ * row-major FP32 DEVICE arrays.  Work runs on a stream of the network's own, ordered after and
+ * before cuda_stream by events. */
+typedef struct jtrlan_mlp jtrlan_mlp;  /* opaque; owned by the library */
+
+int64_t jtrlan_mlp_param_count(int n_in, int width, int n_out);
+
+/* Glorot-uniform weights (splitmix64 on the parameter index and seed), zero biases.
+ * Errors: JTRLAN_EINVAL (sizes outside 1..4096), JTRLAN_ENOMEM, JTRLAN_ECUDA. */
+jtrlan_status jtrlan_mlp_create(int n_in, int width, int n_out, uint64_t seed, void* cuda_stream,
+                                jtrlan_mlp** out);
+
+/* Copy the packed parameters out of / into the network (host or device pointer).  Setting them
+ * also resets the Adam state. */
+jtrlan_status jtrlan_mlp_get_params(jtrlan_mlp* net, float* theta);
+jtrlan_status jtrlan_mlp_set_params(jtrlan_mlp* net, const float* theta);
+
+/* Y = network(X) for N samples (enqueued, no synchronisation). */
+jtrlan_status jtrlan_mlp_forward(jtrlan_mlp* net, const float* X, int N, float* Y);
+
+/* The loss L of the batch and dL/dtheta (packed order) into grad (host or device, may be NULL) and
+ * *loss (host, may be NULL); no parameter change.  Synchronises. */
+jtrlan_status jtrlan_mlp_gradient(jtrlan_mlp* net, const float* X, const float* T, int N, float* grad,
+                                  double* loss);
+
+/* `steps` full-batch Adam steps at learning rate lr.  The step (forward, loss, back-propagation,
+ * update) is captured once per (X, T, N) into a CUDA graph and replayed; loss_hist (host, `steps`
+ * floats, may be NULL) receives the loss before each update.  Synchronises.
+ * Errors: JTRLAN_EINVAL, JTRLAN_ENOMEM, JTRLAN_ECUDA. */
+jtrlan_status jtrlan_mlp_train(jtrlan_mlp* net, const float* X, const float* T, int N, int steps, float lr,
+                               float* loss_hist);
+
+void jtrlan_mlp_destroy(jtrlan_mlp* net);
 
 /* Static text for a status code. */
 const char* jtrlan_status_string(jtrlan_status s);

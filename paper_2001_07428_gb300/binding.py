@@ -23,7 +23,10 @@ JTRLAN_FP64, JTRLAN_MIXED, JTRLAN_MIXED_REORTH = 0, 1, 2
 EXPORTED = ["jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
             "jtrlan_residual_norms_noalloc", "jtrlan_destroy", "jtrlan_status_string", "jtrlan_last_error",
             "jtrlan_batch_create", "jtrlan_batch_set_shape", "jtrlan_batch_tune", "jtrlan_batch_solve",
-            "jtrlan_batch_results", "jtrlan_batch_vectors", "jtrlan_batch_destroy"]
+            "jtrlan_batch_results", "jtrlan_batch_vectors", "jtrlan_batch_destroy", "jtrlan_apply_filter", "jtrlan_bounds",
+            "jtrlan_damped_step", "jtrlan_mlp_param_count", "jtrlan_mlp_create", "jtrlan_mlp_get_params",
+            "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train",
+            "jtrlan_mlp_destroy"]
 NOALLOC_MAX_PARTIALS = 262144   # JTRLAN_NOALLOC_MAX_PARTIALS
 NOALLOC_MAX_COLS = 1024         # JTRLAN_NOALLOC_MAX_COLS
 
@@ -39,7 +42,9 @@ class jtrlan_params(ctypes.Structure):
     _fields_ = [("nev", ctypes.c_int), ("m", ctypes.c_int), ("mwin", ctypes.c_int),
                 ("tol", ctypes.c_double), ("which", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_restarts", ctypes.c_int), ("gs_max_passes", ctypes.c_int),
-                ("v1", ctypes.c_void_p), ("check_jsym", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("v1", ctypes.c_void_p), ("check_jsym", ctypes.c_int), ("profile", ctypes.c_int),
+                ("filter_degree", ctypes.c_int), ("filter_coeffs", ctypes.c_void_p), ("filter_lo", ctypes.c_double),
+                ("filter_hi", ctypes.c_double)]
 
 
 class jtrlan_stats(ctypes.Structure):
@@ -128,9 +133,27 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jtrlan_batch_vectors.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     lib.jtrlan_batch_destroy.argtypes = [ctypes.c_void_p]
     lib.jtrlan_batch_destroy.restype = None
+    lib.jtrlan_apply_filter.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.jtrlan_bounds.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)]
+    lib.jtrlan_damped_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.jtrlan_mlp_param_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.jtrlan_mlp_param_count.restype = ctypes.c_int64
+    lib.jtrlan_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p,
+                                      P(ctypes.c_void_p)]
+    lib.jtrlan_mlp_get_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.jtrlan_mlp_set_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.jtrlan_mlp_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    lib.jtrlan_mlp_gradient.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, P(ctypes.c_double)]
+    lib.jtrlan_mlp_train.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_float, ctypes.c_void_p]
+    lib.jtrlan_mlp_destroy.argtypes = [ctypes.c_void_p]
+    lib.jtrlan_mlp_destroy.restype = None
     for f in ("jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
               "jtrlan_residual_norms_noalloc", "jtrlan_batch_create", "jtrlan_batch_set_shape",
-              "jtrlan_batch_tune", "jtrlan_batch_solve", "jtrlan_batch_results", "jtrlan_batch_vectors"):
+              "jtrlan_batch_tune", "jtrlan_batch_solve", "jtrlan_batch_results", "jtrlan_batch_vectors",
+              "jtrlan_apply_filter", "jtrlan_bounds", "jtrlan_damped_step", "jtrlan_mlp_create", "jtrlan_mlp_get_params",
+              "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -227,6 +250,61 @@ def jtrlan_batch_destroy(b):
         load().jtrlan_batch_destroy(b)
 
 
+def jtrlan_apply_filter(ctx, x_ptr: int, y_ptr: int):
+    _check(load().jtrlan_apply_filter(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr)))
+
+
+def jtrlan_bounds(ctx, steps: int):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(load().jtrlan_bounds(ctx, int(steps), ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def jtrlan_damped_step(tau_ptr: int, count: int, degree: int, out_ptr: int, stream: int = 0):
+    _check(load().jtrlan_damped_step(ctypes.c_void_p(tau_ptr), int(count), int(degree), ctypes.c_void_p(out_ptr),
+                                     ctypes.c_void_p(stream)))
+
+
+def jtrlan_mlp_param_count(n_in: int, width: int, n_out: int) -> int:
+    return int(load().jtrlan_mlp_param_count(int(n_in), int(width), int(n_out)))
+
+
+def jtrlan_mlp_create(n_in: int, width: int, n_out: int, seed: int, stream: int = 0):
+    net = ctypes.c_void_p()
+    _check(load().jtrlan_mlp_create(int(n_in), int(width), int(n_out), ctypes.c_uint64(seed), ctypes.c_void_p(stream),
+                                    ctypes.byref(net)))
+    return net
+
+
+def jtrlan_mlp_get_params(net, theta_ptr):
+    _check(load().jtrlan_mlp_get_params(net, theta_ptr))
+
+
+def jtrlan_mlp_set_params(net, theta_ptr):
+    _check(load().jtrlan_mlp_set_params(net, theta_ptr))
+
+
+def jtrlan_mlp_forward(net, x_ptr: int, N: int, y_ptr: int):
+    _check(load().jtrlan_mlp_forward(net, ctypes.c_void_p(x_ptr), int(N), ctypes.c_void_p(y_ptr)))
+
+
+def jtrlan_mlp_gradient(net, x_ptr: int, t_ptr: int, N: int, grad_ptr) -> float:
+    loss = ctypes.c_double()
+    _check(load().jtrlan_mlp_gradient(net, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(N), grad_ptr,
+                                      ctypes.byref(loss)))
+    return loss.value
+
+
+def jtrlan_mlp_train(net, x_ptr: int, t_ptr: int, N: int, steps: int, lr: float, hist_ptr):
+    _check(load().jtrlan_mlp_train(net, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(N), int(steps),
+                                   ctypes.c_float(lr), hist_ptr))
+
+
+def jtrlan_mlp_destroy(net):
+    if net:
+        load().jtrlan_mlp_destroy(net)
+
+
 # ---------------------------------------------------------------- builders for the structs
 def stencil_operator(dims, m0, kappa, U_ptr, W_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
     op = jtrlan_operator()
@@ -248,7 +326,8 @@ def dense_operator(n, a11_ptr, a12_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
 
 
 def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_restarts=0,
-           gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0) -> jtrlan_params:
+           gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0, filter_coeffs=None, filter_window=None) -> jtrlan_params:
+    """filter_coeffs: a float64 numpy array g_0..g_d (kept alive on the struct until create copies it)."""
     p = jtrlan_params()
     p.nev, p.m, p.mwin, p.tol = int(nev), int(m), int(mwin), float(tol)
     p.which, p.precision = int(which), int(precision)
@@ -256,4 +335,11 @@ def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_
     p.v1 = v1_ptr
     p.check_jsym = int(check_jsym)
     p.profile = int(profile)
+    if filter_coeffs is not None:
+        import numpy as np
+        g = np.ascontiguousarray(filter_coeffs, dtype=np.float64)
+        p._filter_keep = g
+        p.filter_degree = len(g) - 1
+        p.filter_coeffs = g.ctypes.data
+        p.filter_lo, p.filter_hi = float(filter_window[0]), float(filter_window[1])
     return p

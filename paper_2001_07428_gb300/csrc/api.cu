@@ -44,7 +44,7 @@ __global__ void c64_to_c128_kernel(const float2* in, double2* out, int64_t count
 }
 
 const char* kTagNames[K_NTAGS] = {"matvec", "gs_first", "gs_reduce", "gs_update", "gs_dot", "gs_normalize",
-                                  "ritz", "rotate", "resid", "shrink", "other", "ritz_fallback"};
+                                  "ritz", "rotate", "resid", "shrink", "other", "ritz_fallback", "filter"};
 
 // Optional per-launch CUDA-event timing, harvested at the host synchronisation points.
 struct Profiler {
@@ -103,6 +103,8 @@ struct Phase {
   double* alpha_part = nullptr;
   double* resid_part = nullptr;
   int mv_nblk = 0;
+  int which = JTRLAN_SMALLEST;  // the wanted end of this phase's operator
+  bool filtered = false;        // the Lanczos product is B = p(A) (FP32 phase of JTRLAN_MIXED)
 };
 
 }  // namespace
@@ -145,6 +147,9 @@ struct jtrlan_ctx {
   int* h_order = nullptr;
   double* h_misc = nullptr;
   int gs_nblk = 0, gs_rpb = 0;
+  std::vector<double> fcoef;       // filter coefficients g_0..g_d
+  double fc = 0.0, fe = 1.0;       // window centre and half-width
+  void* fbuf[3] = {nullptr, nullptr, nullptr};   // A t, and the two recurrence vectors
   Profiler prof;
   double work_base[3] = {};        // device work counters carried across solve phases
   int fallback_base = 0;
@@ -234,6 +239,12 @@ jtrlan_status validate(const jtrlan_operator* op, const jtrlan_params* p) {
     return fail(JTRLAN_EINVAL, "unknown precision");
   if (p->gs_max_passes < 0 || p->gs_max_passes > 7) return fail(JTRLAN_EINVAL, "gs_max_passes must be 0..7");
   if (p->max_restarts < 0) return fail(JTRLAN_EINVAL, "max_restarts must be >= 0");
+  if (p->filter_degree < 0 || p->filter_degree > 1024) return fail(JTRLAN_EINVAL, "filter_degree must be 0..1024");
+  if (p->filter_degree > 0) {
+    if (p->precision != JTRLAN_MIXED) return fail(JTRLAN_EINVAL, "the filter runs in the FP32 phase of JTRLAN_MIXED");
+    if (!p->filter_coeffs) return fail(JTRLAN_EINVAL, "null filter_coeffs");
+    if (!(p->filter_lo < p->filter_hi)) return fail(JTRLAN_EINVAL, "need filter_lo < filter_hi");
+  }
   return JTRLAN_OK;
 }
 
@@ -329,10 +340,22 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
     }
     if (prm->precision == JTRLAN_MIXED) {
       JT_TRY(make_phase(c->p32, sizeof(float2)));
+      if (prm->filter_degree > 0) {   // B = p(A) in the FP32 phase: largest p wanted
+        c->p32.filtered = true;
+        c->p32.which = JTRLAN_LARGEST;
+        c->fcoef.assign(prm->filter_coeffs, prm->filter_coeffs + prm->filter_degree + 1);
+        c->fc = 0.5 * (prm->filter_lo + prm->filter_hi);
+        c->fe = 0.5 * (prm->filter_hi - prm->filter_lo);
+        for (int b = 0; b < 3; ++b) JT_TRY(c->dalloc(&c->fbuf[b], (size_t)c->n * sizeof(float2)));
+        if (cheb_blocks(c->n) > c->p32.mv_nblk)
+          JT_TRY(c->dalloc(&c->p32.alpha_part, (size_t)cheb_blocks(c->n) * sizeof(double2)));
+      }
     } else {
       c->p32.mv_nblk = matvec_blocks(q);
     }
   }
+  c->p64.which = c->pdf.which = prm->which;
+  if (!c->p32.filtered) c->p32.which = prm->which;
   JT_TRY(c->dalloc(&c->T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
   JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));
   JT_TRY(c->dalloc(&c->Z, (size_t)m * m * sizeof(double)));
@@ -387,6 +410,80 @@ inline void* col(void* base, int64_t n, int j, size_t cs) { return (char*)base +
     c->nl[(tag)] += 1;                     \
   } while (0)
 
+// y = p(A) v by the Chebyshev recurrence (filter.cu): d products of A and d recurrence steps; the
+// last step leaves the alpha partials of conj(v) y in part (cheb_blocks(n) of them) if given.
+template <typename R>
+jtrlan_status filter_apply(jtrlan_ctx* c, Phase& ph, const void* v, void* y, double* part) {
+  using C = cplx<R>;
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  const int d = (int)c->fcoef.size() - 1;
+  const double* g = c->fcoef.data();
+  void* ax = c->fbuf[0];
+  void* B[2] = {c->fbuf[1], c->fbuf[2]};
+  LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)v, (C*)ax, MV_PLAIN, nullptr, nullptr, nullptr, 0, 0, nullptr, s));
+  LAUNCH(K_FILTER, launch_cheb_step<R>(ax, v, nullptr, B[1], y, v, n, c->fc, 1.0 / c->fe, 0.0, g[1], g[0], 1,
+                                       d == 1 ? part : nullptr, s));
+  for (int k = 2; k <= d; ++k) {
+    const void* tcur = B[(k - 1) & 1];                 // T_{k-1}
+    const void* tprev = k == 2 ? v : B[k & 1];         // T_{k-2}
+    void* tnext = B[k & 1];                            // T_k (over T_{k-2} from k = 3 on)
+    LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)tcur, (C*)ax, MV_PLAIN, nullptr, nullptr, nullptr, 0, 0,
+                                      nullptr, s));
+    LAUNCH(K_FILTER, launch_cheb_step<R>(ax, tcur, tprev, tnext, y, v, n, c->fc, 2.0 / c->fe, 1.0, g[k], 0.0, 0,
+                                         k == d ? part : nullptr, s));
+  }
+  return JTRLAN_OK;
+}
+
+// Algorithm 2 steps j0 .. j1-1 of the phase (products, alpha, Gram-Schmidt against V and W with the
+// sqrt(2) test, normalisation), enqueued without host synchronisation.  With `filtered` the product
+// is B = p(A).
+template <typename R>
+jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1, bool filtered) {
+  using C = cplx<R>;
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  const size_t cs = ph.cs;
+  if (ph.df) LAUNCH(K_OTHER, launch_fp64_from_df(col(ph.V, n, j0, cs), ph.x, n, s));   // v_j0 in FP64
+  const int mv_parts = filtered ? cheb_blocks(n) : ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk;
+  for (int j = j0; j < j1; ++j) {
+    if (filtered) {
+      JT_TRY(filter_apply<R>(c, ph, col(ph.V, n, j, cs), ph.y, ph.alpha_part));
+    } else if (ph.dfmv) {   // compensated FP32 on the (hi, lo) column and links, FP64 result
+      LAUNCH(K_MATVEC, launch_matvec_df(ph.opdf, col(ph.V, n, j, cs), ph.y, ph.alpha_part, s));
+    } else {
+      const void* vj = ph.df ? ph.x : col(ph.V, n, j, cs);
+      LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)vj, (C*)ph.y, MV_ALPHA, ph.alpha_part,
+                                        nullptr, nullptr, 0, 0, nullptr, s));
+    }
+    a.j = j;
+    if (ph.df) {
+      // compensated FP32 reorthogonalisation of an FP64 vector against a (hi, lo) basis; see gsdf.cu
+      LAUNCH(K_GS_FIRST, launch_gsdf_first(a, ph.x, (const double2*)ph.alpha_part, mv_parts, s));
+      LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
+      LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
+      for (int pass = 2; pass <= c->gs_passes; ++pass) {
+        LAUNCH(K_GS_DOT, launch_gsdf_dot(a, pass, s));
+        LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
+        LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
+      }
+      LAUNCH(K_GS_NORMALIZE, launch_gsdf_normalize(a, ph.x, s));
+    } else {
+      LAUNCH(K_GS_FIRST, launch_gs_first<R>(a, (const double2*)ph.alpha_part, mv_parts, s));
+      LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
+      LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
+      for (int pass = 2; pass <= c->gs_passes; ++pass) {
+        LAUNCH(K_GS_DOT, launch_gs_dot<R>(a, pass, s));
+        LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
+        LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
+      }
+      LAUNCH(K_GS_NORMALIZE, launch_gs_normalize<R>(a, s));
+    }
+  }
+  return JTRLAN_OK;
+}
+
 // Algorithm 1 (TRLAN-JSYM) in working precision R from the start vector in ph.V[:, 0] (already
 // normalised), until nev pairs have true residual < tol (tol_rel_tmax > 0: the phase tolerance is
 // max(tol, tol_rel_tmax * max|t|), for the FP32 phase).  On success the converged Ritz vectors
@@ -416,47 +513,15 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
   *icnv_out = 0;
   for (int restart = 0; restart < max_restarts; ++restart) {
     // ---- Algorithm 2: m - k Lanczos steps, no host synchronisation inside
-    if (ph.df) LAUNCH(K_OTHER, launch_fp64_from_df(col(ph.V, n, k, cs), ph.x, n, s));   // v_k in FP64
-    const int mv_parts = ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk;
-    for (int j = k; j < m; ++j) {
-      if (ph.dfmv) {   // compensated FP32 on the (hi, lo) column and links, FP64 result
-        LAUNCH(K_MATVEC, launch_matvec_df(ph.opdf, col(ph.V, n, j, cs), ph.y, ph.alpha_part, s));
-      } else {
-        const void* vj = ph.df ? ph.x : col(ph.V, n, j, cs);
-        LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)vj, (C*)ph.y, MV_ALPHA, ph.alpha_part,
-                                          nullptr, nullptr, 0, 0, nullptr, s));
-      }
-      a.j = j;
-      if (ph.df) {
-        // compensated FP32 reorthogonalisation of an FP64 vector against a (hi, lo) basis; see gsdf.cu
-        LAUNCH(K_GS_FIRST, launch_gsdf_first(a, ph.x, (const double2*)ph.alpha_part, mv_parts, s));
-        LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
-        LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
-        for (int pass = 2; pass <= c->gs_passes; ++pass) {
-          LAUNCH(K_GS_DOT, launch_gsdf_dot(a, pass, s));
-          LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
-          LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
-        }
-        LAUNCH(K_GS_NORMALIZE, launch_gsdf_normalize(a, ph.x, s));
-      } else {
-        LAUNCH(K_GS_FIRST, launch_gs_first<R>(a, (const double2*)ph.alpha_part, ph.mv_nblk, s));
-        LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
-        LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
-        for (int pass = 2; pass <= c->gs_passes; ++pass) {
-          LAUNCH(K_GS_DOT, launch_gs_dot<R>(a, pass, s));
-          LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
-          LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
-        }
-        LAUNCH(K_GS_NORMALIZE, launch_gs_normalize<R>(a, s));
-      }
-    }
-    stt.n_matvec += m - k;
-    c->work[K_MATVEC] += (double)(m - k) * mv_units;
+    JT_TRY(lanczos_steps<R>(c, ph, a, k, m, ph.filtered));
+    const int per_step = ph.filtered ? (int)c->fcoef.size() - 1 : 1;   // products of A per Lanczos step
+    stt.n_matvec += (int64_t)(m - k) * per_step;
+    c->work[K_MATVEC] += (double)(m - k) * per_step * mv_units;
     stt.n_restarts += 1;
     // ---- Rayleigh-Ritz (FP64): T_m = Z Lambda Z^T, the kk wanted pairs; V_m Z into Vtmp
-    LAUNCH(K_RITZ, launch_ritz(c->T, ldt, m, k, kk, c->prm.which, c->lam, c->Z, c->ritz_flags, s));
+    LAUNCH(K_RITZ, launch_ritz(c->T, ldt, m, k, kk, ph.which, c->lam, c->Z, c->ritz_flags, s));
     c->nl[K_RITZ] += 1;  // two kernels: bisection + inverse iteration, checks
-    LAUNCH(K_RITZ_FALLBACK, launch_ritz_fallback(c->T, ldt, m, c->prm.which, c->lam, c->Z, c->work_ritz(),
+    LAUNCH(K_RITZ_FALLBACK, launch_ritz_fallback(c->T, ldt, m, ph.which, c->lam, c->Z, c->work_ritz(),
                                                  c->ritz_flags, &c->st->n_ritz_fallbacks, s));
     // V_m Z, first the nev candidate columns (the rest once k of eq. (29) is known)
     const size_t tcs = ph.df ? sizeof(double2) : cs;   // element size of Vtmp
@@ -497,6 +562,11 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
       res_est[i] = std::fabs(arrow[i]);
       conv[i] = 0;                            // is_convd reset every outer iteration
       if (!(res_est[i] < tol_ph)) continue;
+      if (ph.filtered) {   // B = p(A): judged by the estimate; the unfiltered phase certifies
+        res[i] = res_est[i];
+        conv[i] = 1;
+        continue;
+      }
       // A pair locked at the previous restart is decoupled in T-bar (t_{m+1,i} = 0), so the
       // Rayleigh-Ritz step returns it unchanged: keep its verified residual instead of another
       // product (reading R6b).
@@ -582,6 +652,48 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
   c->fallback_base = stt.n_ritz_fallbacks;
   c->gs_pass_base = 0;
   if (icnv != nev) return fail(JTRLAN_ENOCONV, "max_restarts reached before nev pairs converged");
+  return JTRLAN_OK;
+}
+
+// Spectral bounds from `steps` unrestarted Lanczos steps on A (see jtrlan_bounds).
+jtrlan_status bounds_impl(jtrlan_ctx* c, int steps, double* lo, double* hi) {
+  if (steps < 2 || steps > c->m) return fail(JTRLAN_EINVAL, "need 2 <= steps <= m");
+  const bool fp32 = c->prm.precision == JTRLAN_MIXED;
+  Phase& ph = fp32 ? c->p32 : c->mixed ? c->pdf : c->p64;
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  const int ldt = c->m + 1;
+  c->prof.used = 0;
+  JT_CUDA(cudaMemsetAsync(c->st, 0, sizeof(StepState), s));
+  JT_CUDA(cudaMemsetAsync(c->T, 0, (size_t)ldt * ldt * sizeof(double), s));
+  const uint64_t seed = 0xb07d5ull;
+  if (ph.df) {
+    LAUNCH(K_OTHER, launch_fill_random<double>(ph.x, n, seed, s));
+    LAUNCH(K_OTHER, launch_normalize_col<double>(ph.x, n, c->part_nrm, c->gs_nblk, s));
+    LAUNCH(K_OTHER, launch_df_from_fp64(ph.x, ph.V, n, s));
+  } else if (fp32) {
+    LAUNCH(K_OTHER, launch_fill_random<float>(ph.V, n, seed, s));
+    LAUNCH(K_OTHER, launch_normalize_col<float>(ph.V, n, c->part_nrm, c->gs_nblk, s));
+  } else {
+    LAUNCH(K_OTHER, launch_fill_random<double>(ph.V, n, seed, s));
+    LAUNCH(K_OTHER, launch_normalize_col<double>(ph.V, n, c->part_nrm, c->gs_nblk, s));
+  }
+  GSArgs a{};
+  a.V = ph.V; a.n = n; a.h = c->h; a.y = ph.y; a.part_dot = c->part_dot; a.part_nrm = c->part_nrm;
+  a.coef = c->coef; a.st = c->st; a.T = c->T; a.ldt = ldt; a.m = c->m; a.nblk = c->gs_nblk;
+  a.rows_per_block = c->gs_rpb;
+  if (fp32) JT_TRY(lanczos_steps<float>(c, ph, a, 0, steps, false));
+  else JT_TRY(lanczos_steps<double>(c, ph, a, 0, steps, false));
+  LAUNCH(K_RITZ, launch_ritz(c->T, ldt, steps, 0, steps, JTRLAN_SMALLEST, c->lam, c->Z, c->ritz_flags, s));
+  LAUNCH(K_RITZ_FALLBACK, launch_ritz_fallback(c->T, ldt, steps, JTRLAN_SMALLEST, c->lam, c->Z, c->work_ritz(),
+                                               c->ritz_flags, &c->st->n_ritz_fallbacks, s));
+  LAUNCH(K_OTHER, launch_report(c->lam, c->Z, steps, c->T, ldt, c->st, c->d_rep, s));
+  JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * steps + 8) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  JT_CUDA(cudaStreamSynchronize(s));
+  JT_CUDA(c->prof.harvest());
+  if (c->h_rep[2 * steps + 1] != 0.0) return fail(JTRLAN_EBREAKDOWN, "Lanczos breakdown while estimating bounds");
+  *lo = c->h_rep[0];
+  *hi = c->h_rep[steps - 1] + std::fabs(c->h_rep[2 * steps]);
   return JTRLAN_OK;
 }
 
@@ -750,6 +862,26 @@ jtrlan_status jtrlan_get_profile(jtrlan_ctx* c, jtrlan_profile* out) {
     out->launches[t] = c->nl[t];
     out->work[t] = c->work[t];
   }
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_apply_filter(jtrlan_ctx* c, const void* x, void* y) {
+  if (!c || !x || !y) return fail(JTRLAN_EINVAL, "null argument");
+  if (!c->p32.filtered) return fail(JTRLAN_EINVAL, "the context has no filter");
+  cudaStream_t s = c->stream;
+  JT_TRY(filter_apply<float>(c, c->p32, x, y, nullptr));
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_bounds(jtrlan_ctx* c, int steps, double* lo, double* hi) {
+  if (!c || !lo || !hi) return fail(JTRLAN_EINVAL, "null argument");
+  return bounds_impl(c, steps, lo, hi);
+}
+
+jtrlan_status jtrlan_damped_step(const double* tau, int count, int degree, float* out, void* cuda_stream) {
+  if (count < 0 || degree < 0 || degree > 1024) return fail(JTRLAN_EINVAL, "need count >= 0 and 0 <= degree <= 1024");
+  if (count > 0 && (!tau || !out)) return fail(JTRLAN_EINVAL, "null argument");
+  JT_CUDA(launch_damped_step(tau, count, degree, out, (cudaStream_t)cuda_stream));
   return JTRLAN_OK;
 }
 

@@ -465,6 +465,7 @@ template cudaError_t launch_gs_dot<double>(const GSArgs&, int, cudaStream_t);
 template cudaError_t launch_gs_normalize<double>(const GSArgs&, cudaStream_t);
 template cudaError_t launch_fill_ones<double>(void*, int64_t, cudaStream_t);
 template cudaError_t launch_fill_random<double>(void*, int64_t, uint64_t, cudaStream_t);
+template cudaError_t launch_fill_random<float>(void*, int64_t, uint64_t, cudaStream_t);
 template cudaError_t launch_normalize_col<double>(void*, int64_t, double*, int, cudaStream_t);
 template cudaError_t launch_jsym_check<double>(const void*, const void*, int64_t, double*, cudaStream_t);
 

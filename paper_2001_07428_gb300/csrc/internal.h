@@ -90,7 +90,7 @@ cudaError_t launch_links_df(const void* in, void* out, int64_t vol, cudaStream_t
 // Kernel classes for the optional per-kernel profile.
 enum KernelTag {
   K_MATVEC = 0, K_GS_FIRST, K_GS_REDUCE, K_GS_UPDATE, K_GS_DOT, K_GS_NORMALIZE, K_RITZ, K_ROTATE,
-  K_RESID, K_SHRINK, K_OTHER, K_RITZ_FALLBACK, K_NTAGS
+  K_RESID, K_SHRINK, K_OTHER, K_RITZ_FALLBACK, K_FILTER, K_NTAGS
 };
 template <typename R>
 cudaError_t launch_fill_ones(void* v, int64_t n, cudaStream_t s);
@@ -181,6 +181,19 @@ cudaError_t launch_batch(bool df, const BatchArgs& a, int grid, int threads, cud
 // lo = fl32(x - hi).
 cudaError_t launch_split_df_inplace(void* A, int64_t count, cudaStream_t s);
 cudaError_t launch_c64_to_c128(const void* in, void* out, int64_t count, cudaStream_t s);
+
+// ------------------------------------------------------------------ polynomial filter (filter.cu)
+// One step of the Chebyshev recurrence for B = p(A) = sum_k g_k T_k((A - c I)/e) over n complex
+// entries of type R: t_next = sc (ax - c t_cur) - sp t_prev; acc = g0 v + g t_next (init) or
+// acc += g t_next; t_next may alias t_prev.  part (optional): cheb_blocks(n) double2 partials of
+// conj(v) acc.
+int cheb_blocks(int64_t n);
+template <typename R>
+cudaError_t launch_cheb_step(const void* ax, const void* t_cur, const void* t_prev, void* t_next, void* acc,
+                             const void* v, int64_t n, double c, double sc, double sp, double g, double g0, int init,
+                             double* part, cudaStream_t s);
+// out[i][k] (k <= degree) = Jackson-damped Chebyshev coefficients of the step [x <= tau[i]] (FP32).
+cudaError_t launch_damped_step(const double* tau, int count, int degree, float* out, cudaStream_t s);
 
 // Sets the thread-local text returned by jtrlan_last_error().
 void set_last_error(const char* msg);

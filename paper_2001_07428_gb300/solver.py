@@ -25,15 +25,19 @@ class JTRLan:
 
     def __init__(self, kind, *, nev, m, mwin, tol, which="smallest", dims=None, m0=None, kappa=None,
                  U=None, W=None, A11=None, A12=None, v1=None, max_restarts=0, gs_max_passes=0,
-                 check_jsym=False, profile=False, precision="fp64", device="cuda"):
+                 check_jsym=False, profile=False, precision="fp64", filter_coeffs=None, filter_window=None,
+                 links_dtype="c128", device="cuda"):
         B.load()
         self.device = torch.device(device)
         self.stream = torch.cuda.current_stream(self.device)
         keep = []
         if kind == "stencil":
             Ud, Wd = _dev(U, self.device), _dev(W, self.device)
+            dt = B.JTRLAN_C128
+            if links_dtype == "c64":
+                Ud, Wd, dt = Ud.to(torch.complex64), Wd.to(torch.complex64), B.JTRLAN_C64
             keep += [Ud, Wd]
-            op = B.stencil_operator(dims, m0, kappa, Ud.data_ptr(), Wd.data_ptr())
+            op = B.stencil_operator(dims, m0, kappa, Ud.data_ptr(), Wd.data_ptr(), dtype=dt)
         elif kind == "dense":
             Ad, Bd = _dev(A11, self.device), _dev(A12, self.device)
             keep += [Ad, Bd]
@@ -53,7 +57,7 @@ class JTRLan:
         self.mixed = prec != B.JTRLAN_FP64
         prm = B.params(nev, m, mwin, tol, which=w, precision=prec, max_restarts=max_restarts,
                        gs_max_passes=gs_max_passes, v1_ptr=v1p, check_jsym=int(check_jsym),
-                       profile=int(profile))
+                       profile=int(profile), filter_coeffs=filter_coeffs, filter_window=filter_window)
         self.ctx = B.jtrlan_create(op, prm, self.stream.cuda_stream)
         # jtrlan_create copied the operator; v1 is read at solve time, so it is kept alive.
 
@@ -80,6 +84,17 @@ class JTRLan:
 
     def profile(self) -> dict:
         return B.jtrlan_get_profile(self.ctx)
+
+    def apply_filter(self, x: torch.Tensor) -> torch.Tensor:
+        """y = p(A) x with the context's filter and FP32 operator (complex64)."""
+        x = _dev(x, self.device).to(torch.complex64)
+        y = torch.empty_like(x)
+        B.jtrlan_apply_filter(self.ctx, x.data_ptr(), y.data_ptr())
+        return y
+
+    def bounds(self, steps=20):
+        """(lo, hi): spectral window estimate from `steps` unrestarted Lanczos steps (jtrlan_bounds)."""
+        return B.jtrlan_bounds(self.ctx, steps)
 
     def close(self):
         if getattr(self, "ctx", None):
