@@ -201,9 +201,9 @@ jtrlan_status jtrlan_apply_filter(jtrlan_ctx* ctx, const void* x, void* y);
 /* Spectral bounds for a filter window (the paper has no counterpart): `steps` Lanczos steps of
  * Algorithm 2 on A (full reorthogonalisation, no restart) from a fixed pseudo-random start, in the
  * context's working precision (FP32 for JTRLAN_MIXED), then the Rayleigh-Ritz values of the
- * steps x steps tridiagonal in FP64.  *lo = the smallest Ritz value (an upper bound of lambda_min),
- * *hi = the largest Ritz value + beta_steps (an estimate, not a guarantee, of an upper bound of
- * lambda_max).  2 <= steps <= m.  Synchronises the context stream.  Errors: JTRLAN_EINVAL,
+ * steps x steps tridiagonal in FP64.  *lo = theta_min - |beta_steps z_{steps,min}| (the smallest
+ * Ritz value less its residual bound: an estimate of lambda_min), *hi = theta_max + beta_steps (an
+ * estimate, not a guarantee, of an upper bound of lambda_max).  2 <= steps <= m.  Synchronises the context stream.  Errors: JTRLAN_EINVAL,
  * JTRLAN_EBREAKDOWN, JTRLAN_ECUDA. */
 jtrlan_status jtrlan_bounds(jtrlan_ctx* ctx, int steps, double* lo, double* hi);
 

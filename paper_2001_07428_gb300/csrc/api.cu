@@ -692,8 +692,9 @@ jtrlan_status bounds_impl(jtrlan_ctx* c, int steps, double* lo, double* hi) {
   JT_CUDA(cudaStreamSynchronize(s));
   JT_CUDA(c->prof.harvest());
   if (c->h_rep[2 * steps + 1] != 0.0) return fail(JTRLAN_EBREAKDOWN, "Lanczos breakdown while estimating bounds");
-  *lo = c->h_rep[0];
-  *hi = c->h_rep[steps - 1] + std::fabs(c->h_rep[2 * steps]);
+  const double beta = std::fabs(c->h_rep[2 * steps]);
+  *lo = c->h_rep[0] - beta * std::fabs(c->h_rep[steps]);   // theta_min - |beta z_{steps,1}|
+  *hi = c->h_rep[steps - 1] + beta;
   return JTRLAN_OK;
 }
 

@@ -1,0 +1,158 @@
+"""The learned polynomial filter for the stencil operator (the paper has no filter).
+
+A 3-layer perceptron (width 128, FP32; the library's jtrlan_mlp_* kernels) maps cheap features of a
+problem -- the spectral window estimated by jtrlan_bounds, the lattice parameters m0 and kappa, and
+nev -- to the 65 Chebyshev coefficients g_0..g_64 of a real filter p on that window.  The JTRLAN_MIXED
+solver then runs its FP32 phase on B = p(A) and its second, unfiltered phase certifies every pair with
+the true residual of A, so the plain method is both the judge of the answer and the fallback
+(solve_learned reruns unfiltered if the filtered solve fails).
+
+Training targets come from plain runs of the method: the lowest nev + 1 eigenvalues give the cut
+(lambda_nev + lambda_{nev+1})/2, whose Jackson-damped step (jtrlan_damped_step) is the target.
+
+Everything here is marshalling and bookkeeping on a few scalars per problem; every vector operation,
+the network and its training run in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS = os.path.join(PKG, "filter_mlp.npz")
+DEGREE = 64
+WIDTH = 128
+N_FEATURES = 6
+BOUNDS_STEPS = 30
+NEV_GRID = (8, 10, 12, 16, 20, 25, 30, 40, 50, 60, 70, 80, 90, 100)
+
+
+def window(lo: float, hi: float):
+    """The filter window [a, b]: the bounds estimate widened by 2% below (lo is an estimate)."""
+    return lo - 0.02 * (hi - lo), hi
+
+
+def features(lo, hi, m0, kappa, nev, sites) -> np.ndarray:
+    """Six O(1) inputs of the network."""
+    return np.array([(lo - m0) / 8.0, (hi - m0) / 8.0, m0 - 9.0, (kappa - 0.3) / 0.2,
+                     np.log(nev / sites) / 3.0 + 2.0, np.log(nev) / 2.0 - 1.5], dtype=np.float32)
+
+
+def cut_tau(ev_sorted, nev, a, b) -> float:
+    """Window coordinate of the cut between lambda_nev and lambda_{nev+1}, kept inside (-1, 1)."""
+    cut = 0.5 * (ev_sorted[nev - 1] + ev_sorted[nev])
+    c, e = 0.5 * (a + b), 0.5 * (b - a)
+    return float(np.clip((cut - c) / e, -0.999, 0.999))
+
+
+class FilterNet:
+    """The network on one device (parameters in device memory, kernels of the library)."""
+
+    def __init__(self, theta=None, seed=0, device="cuda"):
+        B.load()
+        self.device = torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device)
+        self.net = B.jtrlan_mlp_create(N_FEATURES, WIDTH, DEGREE + 1, seed, self.stream.cuda_stream)
+        self.P = B.jtrlan_mlp_param_count(N_FEATURES, WIDTH, DEGREE + 1)
+        if theta is not None:
+            th = np.ascontiguousarray(theta, dtype=np.float32)
+            assert th.size == self.P
+            B.jtrlan_mlp_set_params(self.net, th.ctypes.data_as(ctypes.c_void_p))
+
+    @classmethod
+    def load(cls, path=WEIGHTS, device="cuda"):
+        z = np.load(path)
+        return cls(theta=z["theta"], device=device)
+
+    def params(self) -> np.ndarray:
+        th = np.zeros(self.P, dtype=np.float32)
+        B.jtrlan_mlp_get_params(self.net, th.ctypes.data_as(ctypes.c_void_p))
+        return th
+
+    def save(self, path=WEIGHTS, **meta):
+        np.savez(path, theta=self.params(), meta=json.dumps(meta))
+
+    def predict(self, X: np.ndarray) -> np.ndarray:
+        X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float32)
+        Xd = torch.from_numpy(X).to(self.device)
+        Yd = torch.empty((X.shape[0], DEGREE + 1), dtype=torch.float32, device=self.device)
+        B.jtrlan_mlp_forward(self.net, Xd.data_ptr(), X.shape[0], Yd.data_ptr())
+        self.stream.synchronize()
+        return Yd.cpu().numpy().astype(np.float64)
+
+    def train(self, X: np.ndarray, T: np.ndarray, steps: int, lr: float) -> np.ndarray:
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.device)
+        Td = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).to(self.device)
+        hist = np.zeros(steps, dtype=np.float32)
+        B.jtrlan_mlp_train(self.net, Xd.data_ptr(), Td.data_ptr(), X.shape[0], steps, lr,
+                           hist.ctypes.data_as(ctypes.c_void_p))
+        return hist
+
+    def loss(self, X: np.ndarray, T: np.ndarray) -> float:
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.device)
+        Td = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).to(self.device)
+        return B.jtrlan_mlp_gradient(self.net, Xd.data_ptr(), Td.data_ptr(), X.shape[0], None)
+
+    def close(self):
+        if getattr(self, "net", None):
+            B.jtrlan_mlp_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def damped_targets(taus, device="cuda") -> np.ndarray:
+    """Jackson-damped step coefficients for each tau, from the library kernel."""
+    td = torch.from_numpy(np.ascontiguousarray(taus, dtype=np.float64)).to(device)
+    out = torch.empty((len(taus), DEGREE + 1), dtype=torch.float32, device=device)
+    B.jtrlan_damped_step(td.data_ptr(), len(taus), DEGREE, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def stencil_bounds(U, W, dims, m0, kappa, device="cuda"):
+    """(lo, hi) of jtrlan_bounds on the FP32 operator (BOUNDS_STEPS unrestarted Lanczos steps)."""
+    from .solver import JTRLan
+    s = JTRLan(kind="stencil", dims=dims, m0=m0, kappa=kappa, U=U, W=W, nev=1, m=BOUNDS_STEPS + 1, mwin=1,
+               tol=1e-8, precision="mixed", device=device)
+    lo, hi = s.bounds(BOUNDS_STEPS)
+    s.close()
+    return lo, hi
+
+
+def learned_filter(net: FilterNet, U, W, dims, m0, kappa, nev, device="cuda"):
+    """(coefficients, window, features) predicted for one stencil problem."""
+    lo, hi = stencil_bounds(U, W, dims, m0, kappa, device)
+    sites = int(np.prod(dims))
+    f = features(lo, hi, m0, kappa, nev, sites)
+    g = net.predict(f[None, :])[0]
+    return g, window(lo, hi), f
+
+
+def solve_learned(net: FilterNet, U, W, dims, m0, kappa, nev, m, mwin, tol, device="cuda", **kw):
+    """J-TRLan (JTRLAN_MIXED) with the network's filter in the FP32 phase; the unfiltered second phase
+    certifies every pair.  Falls back to the unfiltered solve if the filtered one fails.
+    Returns (solver, stats, filter info)."""
+    from .solver import JTRLan
+    g, win, f = learned_filter(net, U, W, dims, m0, kappa, nev, device)
+    base = dict(kind="stencil", dims=dims, m0=m0, kappa=kappa, U=U, W=W, nev=nev, m=m, mwin=mwin, tol=tol,
+                precision="mixed", device=device, **kw)
+    s = JTRLan(filter_coeffs=g, filter_window=win, **base)
+    try:
+        st = s.solve()
+        return s, st, dict(coeffs=g, window=win, features=f, fallback=False)
+    except B.JTRLanError:
+        s.close()
+        s = JTRLan(**base)
+        st = s.solve()
+        return s, st, dict(coeffs=g, window=win, features=f, fallback=True)
