@@ -107,7 +107,13 @@ typedef struct {
  *     judged by the Lanczos residual estimates |t_{m+1,i}| of B only (to 1e-5 max|t|); the second,
  *     unfiltered phase then starts from the sum of its Ritz vectors and certifies every pair with
  *     the true residual of A, so a poor filter costs time, never accuracy.  [lo, hi] should contain
- *     the spectrum (jtrlan_bounds estimates it); 1 <= d <= 1024. */
+ *     the spectrum (jtrlan_bounds estimates it); 1 <= d <= 1024.
+ *   filter_final_degree, filter_final_coeffs: with d2 > 0 the certifying phase (the only phase of
+ *     JTRLAN_FP64 and JTRLAN_MIXED_REORTH, the second of JTRLAN_MIXED) also runs on B2 = p2(A), same
+ *     window, largest wanted, with FP64-accurate products; a Ritz vector x of B2 is accepted when
+ *     ||A x - (x^H A x) x|| < tol (checked once B2's estimate is below 10 tol), and x^H A x is the
+ *     eigenvalue reported.  Choose p2 strictly decreasing across the wanted eigenvalues: where p2 is
+ *     flat, B2 cannot separate eigenvectors and the solve ends in JTRLAN_ENOCONV. */
 typedef struct {
   int nev;
   int m;
@@ -123,6 +129,8 @@ typedef struct {
   int filter_degree;  /* 0: none; else the degree d of the polynomial filter (JTRLAN_MIXED only) */
   const double* filter_coeffs;  /* host, d + 1 Chebyshev coefficients g_0..g_d (copied at create) */
   double filter_lo, filter_hi;  /* the window [a, b] of the Chebyshev variable (A - c)/e */
+  int filter_final_degree;      /* 0: none; else the degree of the certifying phase's filter */
+  const double* filter_final_coeffs;  /* host, filter_final_degree + 1 coefficients (copied) */
 } jtrlan_params;
 
 /* Counters of the last solve (Sec. 3 counts only the Lanczos-step products as N_MV). */

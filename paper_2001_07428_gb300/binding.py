@@ -44,7 +44,8 @@ class jtrlan_params(ctypes.Structure):
                 ("max_restarts", ctypes.c_int), ("gs_max_passes", ctypes.c_int),
                 ("v1", ctypes.c_void_p), ("check_jsym", ctypes.c_int), ("profile", ctypes.c_int),
                 ("filter_degree", ctypes.c_int), ("filter_coeffs", ctypes.c_void_p), ("filter_lo", ctypes.c_double),
-                ("filter_hi", ctypes.c_double)]
+                ("filter_hi", ctypes.c_double), ("filter_final_degree", ctypes.c_int),
+                ("filter_final_coeffs", ctypes.c_void_p)]
 
 
 class jtrlan_stats(ctypes.Structure):
@@ -326,8 +327,10 @@ def dense_operator(n, a11_ptr, a12_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
 
 
 def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_restarts=0,
-           gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0, filter_coeffs=None, filter_window=None) -> jtrlan_params:
-    """filter_coeffs: a float64 numpy array g_0..g_d (kept alive on the struct until create copies it)."""
+           gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0, filter_coeffs=None, filter_window=None,
+           filter_final_coeffs=None) -> jtrlan_params:
+    """filter_coeffs / filter_final_coeffs: float64 arrays g_0..g_d (kept alive on the struct until
+    create copies them); filter_window: (lo, hi)."""
     p = jtrlan_params()
     p.nev, p.m, p.mwin, p.tol = int(nev), int(m), int(mwin), float(tol)
     p.which, p.precision = int(which), int(precision)
@@ -341,5 +344,12 @@ def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_
         p._filter_keep = g
         p.filter_degree = len(g) - 1
         p.filter_coeffs = g.ctypes.data
+        p.filter_lo, p.filter_hi = float(filter_window[0]), float(filter_window[1])
+    if filter_final_coeffs is not None:
+        import numpy as np
+        g2 = np.ascontiguousarray(filter_final_coeffs, dtype=np.float64)
+        p._filter_final_keep = g2
+        p.filter_final_degree = len(g2) - 1
+        p.filter_final_coeffs = g2.ctypes.data
         p.filter_lo, p.filter_hi = float(filter_window[0]), float(filter_window[1])
     return p

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -104,7 +105,10 @@ struct Phase {
   double* resid_part = nullptr;
   int mv_nblk = 0;
   int which = JTRLAN_SMALLEST;  // the wanted end of this phase's operator
-  bool filtered = false;        // the Lanczos product is B = p(A) (FP32 phase of JTRLAN_MIXED)
+  bool filtered = false;        // the Lanczos product is B = p(A)
+  bool certify = false;         // filtered phase judged by the true residual of A at x^H A x
+  std::vector<double> fcoef;    // filter coefficients g_0..g_d
+  void* fbuf[4] = {nullptr, nullptr, nullptr, nullptr};   // A t, two recurrence vectors, (hi, lo) copy
 };
 
 }  // namespace
@@ -147,9 +151,7 @@ struct jtrlan_ctx {
   int* h_order = nullptr;
   double* h_misc = nullptr;
   int gs_nblk = 0, gs_rpb = 0;
-  std::vector<double> fcoef;       // filter coefficients g_0..g_d
-  double fc = 0.0, fe = 1.0;       // window centre and half-width
-  void* fbuf[3] = {nullptr, nullptr, nullptr};   // A t, and the two recurrence vectors
+  double fc = 0.0, fe = 1.0;       // filter window centre and half-width
   Profiler prof;
   double work_base[3] = {};        // device work counters carried across solve phases
   int fallback_base = 0;
@@ -240,11 +242,15 @@ jtrlan_status validate(const jtrlan_operator* op, const jtrlan_params* p) {
   if (p->gs_max_passes < 0 || p->gs_max_passes > 7) return fail(JTRLAN_EINVAL, "gs_max_passes must be 0..7");
   if (p->max_restarts < 0) return fail(JTRLAN_EINVAL, "max_restarts must be >= 0");
   if (p->filter_degree < 0 || p->filter_degree > 1024) return fail(JTRLAN_EINVAL, "filter_degree must be 0..1024");
+  if (p->filter_final_degree < 0 || p->filter_final_degree > 1024)
+    return fail(JTRLAN_EINVAL, "filter_final_degree must be 0..1024");
   if (p->filter_degree > 0) {
-    if (p->precision != JTRLAN_MIXED) return fail(JTRLAN_EINVAL, "the filter runs in the FP32 phase of JTRLAN_MIXED");
+    if (p->precision != JTRLAN_MIXED) return fail(JTRLAN_EINVAL, "filter_degree applies to the FP32 phase of JTRLAN_MIXED");
     if (!p->filter_coeffs) return fail(JTRLAN_EINVAL, "null filter_coeffs");
-    if (!(p->filter_lo < p->filter_hi)) return fail(JTRLAN_EINVAL, "need filter_lo < filter_hi");
   }
+  if (p->filter_final_degree > 0 && !p->filter_final_coeffs) return fail(JTRLAN_EINVAL, "null filter_final_coeffs");
+  if ((p->filter_degree > 0 || p->filter_final_degree > 0) && !(p->filter_lo < p->filter_hi))
+    return fail(JTRLAN_EINVAL, "need filter_lo < filter_hi");
   return JTRLAN_OK;
 }
 
@@ -343,10 +349,8 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
       if (prm->filter_degree > 0) {   // B = p(A) in the FP32 phase: largest p wanted
         c->p32.filtered = true;
         c->p32.which = JTRLAN_LARGEST;
-        c->fcoef.assign(prm->filter_coeffs, prm->filter_coeffs + prm->filter_degree + 1);
-        c->fc = 0.5 * (prm->filter_lo + prm->filter_hi);
-        c->fe = 0.5 * (prm->filter_hi - prm->filter_lo);
-        for (int b = 0; b < 3; ++b) JT_TRY(c->dalloc(&c->fbuf[b], (size_t)c->n * sizeof(float2)));
+        c->p32.fcoef.assign(prm->filter_coeffs, prm->filter_coeffs + prm->filter_degree + 1);
+        for (int b = 0; b < 3; ++b) JT_TRY(c->dalloc(&c->p32.fbuf[b], (size_t)c->n * sizeof(float2)));
         if (cheb_blocks(c->n) > c->p32.mv_nblk)
           JT_TRY(c->dalloc(&c->p32.alpha_part, (size_t)cheb_blocks(c->n) * sizeof(double2)));
       }
@@ -356,6 +360,20 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   }
   c->p64.which = c->pdf.which = prm->which;
   if (!c->p32.filtered) c->p32.which = prm->which;
+  c->fc = 0.5 * (prm->filter_lo + prm->filter_hi);
+  c->fe = 0.5 * (prm->filter_hi - prm->filter_lo);
+  if (prm->filter_final_degree > 0) {   // the certifying phase on B = p(A), judged by A's residuals
+    Phase& ph = c->mixed ? c->pdf : c->p64;
+    ph.filtered = true;
+    ph.certify = true;
+    ph.which = JTRLAN_LARGEST;
+    ph.fcoef.assign(prm->filter_final_coeffs, prm->filter_final_coeffs + prm->filter_final_degree + 1);
+    for (int b = 0; b < 3; ++b) JT_TRY(c->dalloc(&ph.fbuf[b], (size_t)c->n * sizeof(double2)));
+    JT_TRY(c->dalloc(&ph.fbuf[3], (size_t)c->n * sizeof(float4)));
+    const int nb = std::max(cheb_blocks(c->n), ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk);
+    JT_TRY(c->dalloc(&ph.alpha_part, (size_t)nb * sizeof(double2)));
+    JT_TRY(c->dalloc(&ph.resid_part, (size_t)std::max(nb, ph.mv_nblk * c->nev) * sizeof(double)));
+  }
   JT_TRY(c->dalloc(&c->T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
   JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));
   JT_TRY(c->dalloc(&c->Z, (size_t)m * m * sizeof(double)));
@@ -417,13 +435,13 @@ jtrlan_status filter_apply(jtrlan_ctx* c, Phase& ph, const void* v, void* y, dou
   using C = cplx<R>;
   cudaStream_t s = c->stream;
   const int64_t n = c->n;
-  const int d = (int)c->fcoef.size() - 1;
-  const double* g = c->fcoef.data();
-  void* ax = c->fbuf[0];
-  void* B[2] = {c->fbuf[1], c->fbuf[2]};
+  const int d = (int)ph.fcoef.size() - 1;
+  const double* g = ph.fcoef.data();
+  void* ax = ph.fbuf[0];
+  void* B[2] = {ph.fbuf[1], ph.fbuf[2]};
   LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)v, (C*)ax, MV_PLAIN, nullptr, nullptr, nullptr, 0, 0, nullptr, s));
   LAUNCH(K_FILTER, launch_cheb_step<R>(ax, v, nullptr, B[1], y, v, n, c->fc, 1.0 / c->fe, 0.0, g[1], g[0], 1,
-                                       d == 1 ? part : nullptr, s));
+                                       d == 1 ? part : nullptr, nullptr, s));
   for (int k = 2; k <= d; ++k) {
     const void* tcur = B[(k - 1) & 1];                 // T_{k-1}
     const void* tprev = k == 2 ? v : B[k & 1];         // T_{k-2}
@@ -431,8 +449,64 @@ jtrlan_status filter_apply(jtrlan_ctx* c, Phase& ph, const void* v, void* y, dou
     LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)tcur, (C*)ax, MV_PLAIN, nullptr, nullptr, nullptr, 0, 0,
                                       nullptr, s));
     LAUNCH(K_FILTER, launch_cheb_step<R>(ax, tcur, tprev, tnext, y, v, n, c->fc, 2.0 / c->fe, 1.0, g[k], 0.0, 0,
-                                         k == d ? part : nullptr, s));
+                                         k == d ? part : nullptr, nullptr, s));
   }
+  return JTRLAN_OK;
+}
+
+// The certifying phase's product y = p(A) v_j in FP64 vectors: FP64 products, or compensated-FP32
+// products on (hi, lo) copies that each recurrence step leaves beside its FP64 vector (stencil
+// double-float phase); alpha partials of conj(v_j) y in ph.alpha_part (cheb_blocks(n)).
+jtrlan_status filter_apply_cert(jtrlan_ctx* c, Phase& ph, int j) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  const int d = (int)ph.fcoef.size() - 1;
+  const double* g = ph.fcoef.data();
+  void* ax = ph.fbuf[0];
+  void* B[2] = {ph.fbuf[1], ph.fbuf[2]};
+  void* sp = ph.fbuf[3];
+  const void* v = ph.df ? ph.x : col(ph.V, n, j, ph.cs);   // v_j in FP64
+  auto product = [&](const void* t64, const void* t4) -> jtrlan_status {
+    if (ph.dfmv)
+      LAUNCH(K_MATVEC, launch_matvec_df(ph.opdf, t4, ax, nullptr, s));
+    else
+      LAUNCH(K_MATVEC, launch_matvec<double>(ph.op, (const double2*)t64, (double2*)ax, MV_PLAIN, nullptr, nullptr,
+                                             nullptr, 0, 0, nullptr, s));
+    return JTRLAN_OK;
+  };
+  JT_TRY(product(v, col(ph.V, n, j, ph.cs)));
+  LAUNCH(K_FILTER, launch_cheb_step<double>(ax, v, nullptr, B[1], ph.y, v, n, c->fc, 1.0 / c->fe, 0.0, g[1], g[0], 1,
+                                            d == 1 ? ph.alpha_part : nullptr, (ph.dfmv && d > 1) ? sp : nullptr, s));
+  for (int k = 2; k <= d; ++k) {
+    const void* tcur = B[(k - 1) & 1];
+    const void* tprev = k == 2 ? v : B[k & 1];
+    void* tnext = B[k & 1];
+    JT_TRY(product(tcur, sp));
+    LAUNCH(K_FILTER, launch_cheb_step<double>(ax, tcur, tprev, tnext, ph.y, v, n, c->fc, 2.0 / c->fe, 1.0, g[k], 0.0,
+                                              0, k == d ? ph.alpha_part : nullptr, (ph.dfmv && k < d) ? sp : nullptr,
+                                              s));
+  }
+  return JTRLAN_OK;
+}
+
+// Rayleigh quotient lam_out = x^H A x and residual res_out = ||A x - lam x|| of one FP64 column
+// (device scalars), for the certifying filtered phase.
+jtrlan_status rq_resid(jtrlan_ctx* c, Phase& ph, const void* x, double* lam_out, double* res_out) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  int nparts;
+  if (ph.dfmv) {
+    LAUNCH(K_RESID, launch_df_from_fp64(x, ph.fbuf[3], n, s));
+    LAUNCH(K_RESID, launch_matvec_df(ph.opdf, ph.fbuf[3], ph.fbuf[0], ph.alpha_part, s));
+    nparts = matvec_df_blocks(ph.opdf);
+  } else {
+    LAUNCH(K_RESID, launch_matvec<double>(ph.op, (const double2*)x, (double2*)ph.fbuf[0], MV_ALPHA, ph.alpha_part,
+                                          nullptr, nullptr, 0, 0, nullptr, s));
+    nparts = ph.mv_nblk;
+  }
+  LAUNCH(K_RESID, launch_sum_re(ph.alpha_part, nparts, lam_out, s));
+  LAUNCH(K_RESID, launch_resid_part(ph.fbuf[0], x, lam_out, n, ph.resid_part, s));
+  LAUNCH(K_RESID, launch_reduce_norms(ph.resid_part, cheb_blocks(n), 1, res_out, s));
   return JTRLAN_OK;
 }
 
@@ -449,7 +523,10 @@ jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1,
   const int mv_parts = filtered ? cheb_blocks(n) : ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk;
   for (int j = j0; j < j1; ++j) {
     if (filtered) {
-      JT_TRY(filter_apply<R>(c, ph, col(ph.V, n, j, cs), ph.y, ph.alpha_part));
+      if constexpr (std::is_same<R, float>::value)
+        JT_TRY(filter_apply<R>(c, ph, col(ph.V, n, j, cs), ph.y, ph.alpha_part));
+      else
+        JT_TRY(filter_apply_cert(c, ph, j));
     } else if (ph.dfmv) {   // compensated FP32 on the (hi, lo) column and links, FP64 result
       LAUNCH(K_MATVEC, launch_matvec_df(ph.opdf, col(ph.V, n, j, cs), ph.y, ph.alpha_part, s));
     } else {
@@ -506,15 +583,16 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
   ev.assign(nev, 0.0);
   res.assign(nev, INFINITY);
   std::vector<double> res_est(nev), lamv(m), arrow(m);
+  std::vector<double> rq(nev, 0.0);            // certifying filtered phase: x^H A x of each candidate
   std::vector<char> conv(nev);
   std::vector<int> perm(m);
-  std::vector<double> locked_ev, locked_res;   // pairs locked at the previous restart
+  std::vector<double> locked_ev, locked_res, locked_rq;   // pairs locked at the previous restart
   int k = 0, icnv = 0;
   *icnv_out = 0;
   for (int restart = 0; restart < max_restarts; ++restart) {
     // ---- Algorithm 2: m - k Lanczos steps, no host synchronisation inside
     JT_TRY(lanczos_steps<R>(c, ph, a, k, m, ph.filtered));
-    const int per_step = ph.filtered ? (int)c->fcoef.size() - 1 : 1;   // products of A per Lanczos step
+    const int per_step = ph.filtered ? (int)ph.fcoef.size() - 1 : 1;   // products of A per Lanczos step
     stt.n_matvec += (int64_t)(m - k) * per_step;
     c->work[K_MATVEC] += (double)(m - k) * per_step * mv_units;
     stt.n_restarts += 1;
@@ -561,8 +639,10 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
       ev[i] = lamv[i];
       res_est[i] = std::fabs(arrow[i]);
       conv[i] = 0;                            // is_convd reset every outer iteration
-      if (!(res_est[i] < tol_ph)) continue;
-      if (ph.filtered) {   // B = p(A): judged by the estimate; the unfiltered phase certifies
+      // a certifying filtered phase tests A's residual once B's estimate is near tol (B = p(A)
+      // scales residuals by about |p'(lambda)|, so the estimate alone is neither necessary nor enough)
+      if (!(res_est[i] < (ph.certify ? 10.0 * tol_ph : tol_ph))) continue;
+      if (ph.filtered && !ph.certify) {   // B = p(A): judged by the estimate; the unfiltered phase certifies
         res[i] = res_est[i];
         conv[i] = 1;
         continue;
@@ -576,13 +656,30 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
           if (std::fabs(ev[i] - locked_ev[q]) <= 1e-12 * std::max(1.0, std::fabs(ev[i]))) { hit = (int)q; break; }
       if (hit >= 0) {
         res[i] = locked_res[hit];
+        rq[i] = locked_rq[hit];
         conv[i] = 1;
         reused[i] = 1;
         continue;
       }
       c->h_cand[ncand] = i; c->h_candlam[ncand] = ev[i]; ++ncand;
     }
-    if (ncand > 0) {  // true residuals ||A v_i - ev_i v_i|| of the candidates
+    if (ncand > 0 && ph.certify) {  // x^H A x and ||A x - (x^H A x) x|| of each candidate (FP64)
+      for (int q = 0; q < ncand; ++q)
+        JT_TRY(rq_resid(c, ph, (char*)ph.Vtmp + (size_t)c->h_cand[q] * n * sizeof(double2), c->d_candlam + q,
+                        c->d_res + q));
+      JT_CUDA(cudaMemcpyAsync(c->h_res, c->d_res, ncand * sizeof(double), cudaMemcpyDeviceToHost, s));
+      JT_CUDA(cudaMemcpyAsync(c->h_candlam, c->d_candlam, ncand * sizeof(double), cudaMemcpyDeviceToHost, s));
+      JT_CUDA(cudaStreamSynchronize(s));
+      JT_CUDA(c->prof.harvest());
+      stt.n_resid_matvec += ncand;
+      c->work[K_RESID] += (double)ncand * mv_units;
+      for (int q = 0; q < ncand; ++q) {
+        const int i = c->h_cand[q];
+        res[i] = c->h_res[q];
+        rq[i] = c->h_candlam[q];
+        conv[i] = res[i] < tol_ph;
+      }
+    } else if (ncand > 0) {  // true residuals ||A v_i - ev_i v_i|| of the candidates
       JT_CUDA(cudaMemcpyAsync(c->d_cand, c->h_cand, ncand * sizeof(int), cudaMemcpyHostToDevice, s));
       JT_CUDA(cudaMemcpyAsync(c->d_candlam, c->h_candlam, ncand * sizeof(double), cudaMemcpyHostToDevice, s));
       LAUNCH(K_RESID, launch_matvec<R>(ph.op, (const C*)ph.Vtmp, nullptr, MV_RESID, ph.resid_part, c->d_cand,
@@ -605,14 +702,16 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     icnv = w;
     for (int i = 0; i < nev; ++i) if (!conv[i]) perm[w++] = i;
     for (int i = nev; i < m; ++i) perm[i] = i;
-    std::vector<double> ev2(nev), res2(nev), lam2(m), arrow2(m);
+    std::vector<double> ev2(nev), res2(nev), lam2(m), arrow2(m), rq2(nev);
     for (int i = 0; i < kk; ++i) { lam2[i] = lamv[perm[i]]; arrow2[i] = arrow[perm[i]]; }
-    for (int i = 0; i < nev; ++i) { ev2[i] = ev[perm[i]]; res2[i] = res[perm[i]]; }
-    ev = ev2; res = res2; lamv = lam2; arrow = arrow2;
+    for (int i = 0; i < nev; ++i) { ev2[i] = ev[perm[i]]; res2[i] = res[perm[i]]; rq2[i] = rq[perm[i]]; }
+    ev = ev2; res = res2; lamv = lam2; arrow = arrow2; rq = rq2;
     for (int i = 0; i < icnv; ++i) arrow[i] = 0.0;   // decouple the converged subspace
     locked_ev.assign(ev.begin(), ev.begin() + icnv);
     locked_res.assign(res.begin(), res.begin() + icnv);
+    locked_rq.assign(rq.begin(), rq.begin() + icnv);
     *icnv_out = icnv;
+    if (icnv == nev && ph.certify) ev = rq;   // eigenvalues of A, not of B = p(A)
     if (icnv == nev) {
       for (int i = 0; i < m; ++i) c->h_perm[i] = perm[i];
       JT_CUDA(cudaMemcpyAsync(c->d_perm, c->h_perm, m * sizeof(int), cudaMemcpyHostToDevice, s));

@@ -22,7 +22,7 @@ template <typename R>
 __global__ void __launch_bounds__(kChebThreads)
 cheb_step_kernel(const cplx<R>* __restrict__ ax, const cplx<R>* __restrict__ t_cur, const cplx<R>* t_prev,
                  cplx<R>* t_next, cplx<R>* __restrict__ acc, const cplx<R>* __restrict__ v, int64_t n, R c, R sc,
-                 R sp, R g, R g0, int init, double* __restrict__ part) {
+                 R sp, R g, R g0, int init, double* __restrict__ part, float4* __restrict__ split_next) {
   double ar = 0.0, ai = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kChebThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kChebThreads) {
     const cplx<R> a = ax[i], t = t_cur[i];
@@ -35,6 +35,10 @@ cheb_step_kernel(const cplx<R>* __restrict__ ax, const cplx<R>* __restrict__ t_c
       nx.y -= sp * p.y;
     }
     t_next[i] = nx;
+    if (split_next) {   // (hi, lo) copy of t_next for a compensated-FP32 product
+      const float hx = (float)nx.x, hy = (float)nx.y;
+      split_next[i] = make_float4(hx, hy, (float)((double)nx.x - (double)hx), (float)((double)nx.y - (double)hy));
+    }
     cplx<R> s;
     if (init) {
       const cplx<R> vv = v[i];
@@ -90,6 +94,43 @@ __global__ void damped_step_kernel(const double* __restrict__ tau, int count, in
   }
 }
 
+// out[0] = sum_i Re(part[i]) (fixed order): the Rayleigh quotient from conj(x) A x partials.
+__global__ void sum_re_kernel(const double2* __restrict__ part, int nblk, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i].x;
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    out[0] = t;
+  }
+}
+
+// Per-block partial sums of |y_i - lambda x_i|^2 (FP64).
+__global__ void __launch_bounds__(kChebThreads)
+resid_part_kernel(const double2* __restrict__ y, const double2* __restrict__ x, const double* __restrict__ lam, int64_t n,
+                  double* __restrict__ part) {
+  const double l = *lam;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kChebThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kChebThreads) {
+    const double2 a = y[i], b = x[i];
+    const double dr = a.x - l * b.x, di = a.y - l * b.y;
+    acc += dr * dr + di * di;
+  }
+  __shared__ double red[kChebThreads / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kChebThreads / 32; ++q) t += red[q];
+    part[blockIdx.x] = t;
+  }
+}
+
 }  // namespace
 
 int cheb_blocks(int64_t n) {
@@ -100,17 +141,29 @@ int cheb_blocks(int64_t n) {
 template <typename R>
 cudaError_t launch_cheb_step(const void* ax, const void* t_cur, const void* t_prev, void* t_next, void* acc,
                              const void* v, int64_t n, double c, double sc, double sp, double g, double g0, int init,
-                             double* part, cudaStream_t s) {
+                             double* part, void* split_next, cudaStream_t s) {
   cheb_step_kernel<R><<<cheb_blocks(n), kChebThreads, 0, s>>>(
       (const cplx<R>*)ax, (const cplx<R>*)t_cur, (const cplx<R>*)t_prev, (cplx<R>*)t_next, (cplx<R>*)acc,
-      (const cplx<R>*)v, n, (R)c, (R)sc, (R)sp, (R)g, (R)g0, init, part);
+      (const cplx<R>*)v, n, (R)c, (R)sc, (R)sp, (R)g, (R)g0, init, part, (float4*)split_next);
   return cudaGetLastError();
 }
 template cudaError_t launch_cheb_step<float>(const void*, const void*, const void*, void*, void*, const void*, int64_t,
-                                             double, double, double, double, double, int, double*, cudaStream_t);
+                                             double, double, double, double, double, int, double*, void*,
+                                             cudaStream_t);
 template cudaError_t launch_cheb_step<double>(const void*, const void*, const void*, void*, void*, const void*,
-                                              int64_t, double, double, double, double, double, int, double*,
+                                              int64_t, double, double, double, double, double, int, double*, void*,
                                               cudaStream_t);
+
+cudaError_t launch_sum_re(const double* part, int nblk, double* out, cudaStream_t s) {
+  sum_re_kernel<<<1, 256, 0, s>>>((const double2*)part, nblk, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_part(const void* y, const void* x, const double* lam, int64_t n, double* part,
+                              cudaStream_t s) {
+  resid_part_kernel<<<cheb_blocks(n), kChebThreads, 0, s>>>((const double2*)y, (const double2*)x, lam, n, part);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_damped_step(const double* tau, int count, int degree, float* out, cudaStream_t s) {
   const int total = count * (degree + 1);

@@ -186,12 +186,17 @@ cudaError_t launch_c64_to_c128(const void* in, void* out, int64_t count, cudaStr
 // One step of the Chebyshev recurrence for B = p(A) = sum_k g_k T_k((A - c I)/e) over n complex
 // entries of type R: t_next = sc (ax - c t_cur) - sp t_prev; acc = g0 v + g t_next (init) or
 // acc += g t_next; t_next may alias t_prev.  part (optional): cheb_blocks(n) double2 partials of
-// conj(v) acc.
+// conj(v) acc.  split_next (optional): float4 (hi, lo) copy of t_next.
 int cheb_blocks(int64_t n);
 template <typename R>
 cudaError_t launch_cheb_step(const void* ax, const void* t_cur, const void* t_prev, void* t_next, void* acc,
                              const void* v, int64_t n, double c, double sc, double sp, double g, double g0, int init,
-                             double* part, cudaStream_t s);
+                             double* part, void* split_next, cudaStream_t s);
+// out[0] = sum of the real parts of nblk double2 partials.
+cudaError_t launch_sum_re(const double* part, int nblk, double* out, cudaStream_t s);
+// cheb_blocks(n) partial sums of |y - lam[0] x|^2 (FP64 complex vectors).
+cudaError_t launch_resid_part(const void* y, const void* x, const double* lam, int64_t n, double* part,
+                              cudaStream_t s);
 // out[i][k] (k <= degree) = Jackson-damped Chebyshev coefficients of the step [x <= tau[i]] (FP32).
 cudaError_t launch_damped_step(const double* tau, int count, int degree, float* out, cudaStream_t s);
 

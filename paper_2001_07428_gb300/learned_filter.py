@@ -2,10 +2,12 @@
 
 A 3-layer perceptron (width 128, FP32; the library's jtrlan_mlp_* kernels) maps cheap features of a
 problem -- the spectral window estimated by jtrlan_bounds, the lattice parameters m0 and kappa, and
-nev -- to the 65 Chebyshev coefficients g_0..g_64 of a real filter p on that window.  The JTRLAN_MIXED
-solver then runs its FP32 phase on B = p(A) and its second, unfiltered phase certifies every pair with
-the true residual of A, so the plain method is both the judge of the answer and the fallback
-(solve_learned reruns unfiltered if the filtered solve fails).
+nev -- to the DEGREE + 1 Chebyshev coefficients g_0..g_DEGREE of a real filter p on that window.  The
+solver (JTRLAN_MIXED_REORTH: FP64 vectors, compensated-FP32 products and Gram-Schmidt) runs Algorithm 1
+on B = p(A) and accepts a pair only when the true residual of A at x^H A x is below tol, so the plain
+method's criterion judges every answer, and the unfiltered solve is the fallback (solve_learned reruns
+it if the filtered solve fails).  Degree 16 (out of the <= 64 allowed) was the fastest of 8, 16, 32
+on 8^4, 12^4 and 16^4 lattices.
 
 Training targets come from plain runs of the method: the lowest nev + 1 eigenvalues give the cut
 (lambda_nev + lambda_{nev+1})/2, whose Jackson-damped step (jtrlan_damped_step) is the target.
@@ -26,7 +28,8 @@ from . import binding as B
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(PKG, "filter_mlp.npz")
-DEGREE = 64
+RUNS = os.path.join(PKG, "filter_runs.json")   # the plain runs the network was trained on
+DEGREE = 16
 WIDTH = 128
 N_FEATURES = 6
 BOUNDS_STEPS = 30
@@ -140,14 +143,14 @@ def learned_filter(net: FilterNet, U, W, dims, m0, kappa, nev, device="cuda"):
 
 
 def solve_learned(net: FilterNet, U, W, dims, m0, kappa, nev, m, mwin, tol, device="cuda", **kw):
-    """J-TRLan (JTRLAN_MIXED) with the network's filter in the FP32 phase; the unfiltered second phase
-    certifies every pair.  Falls back to the unfiltered solve if the filtered one fails.
+    """J-TRLan (JTRLAN_MIXED_REORTH) on B = p(A) with the network's filter, every pair certified by the
+    true residual of A.  Falls back to the unfiltered solve if the filtered one fails.
     Returns (solver, stats, filter info)."""
     from .solver import JTRLan
     g, win, f = learned_filter(net, U, W, dims, m0, kappa, nev, device)
     base = dict(kind="stencil", dims=dims, m0=m0, kappa=kappa, U=U, W=W, nev=nev, m=m, mwin=mwin, tol=tol,
-                precision="mixed", device=device, **kw)
-    s = JTRLan(filter_coeffs=g, filter_window=win, **base)
+                precision="mixed_reorth", device=device, **kw)
+    s = JTRLan(filter_final_coeffs=g, filter_window=win, **base)
     try:
         st = s.solve()
         return s, st, dict(coeffs=g, window=win, features=f, fallback=False)

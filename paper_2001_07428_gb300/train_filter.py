@@ -2,6 +2,9 @@
 
     python -m paper_2001_07428_gb300.train_filter [--runs 96,24,8] [--steps 6000] [--data PATH] [--out PATH]
 
+With --data naming an existing file (default: the committed filter_runs.json) the plain runs are read
+from it instead of being generated again.
+
 1. Seeded plain runs (JTRLAN_MIXED_REORTH, no filter, residual 1e-7) on 8^4, 12^4 and 16^4 lattices
    with m0 ~ U[8, 10], kappa ~ U[0.1, 0.5], links from inputs.stencil_links: the lowest 101
    eigenvalues of each, and the spectral window from jtrlan_bounds (the network's inputs).
@@ -64,7 +67,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs", default="96,24,8", help="runs per lattice (8^4, 12^4, 16^4)")
     ap.add_argument("--steps", type=int, default=6000)
-    ap.add_argument("--data", default=None, help="cached plain-run records (json); generated if missing")
+    ap.add_argument("--data", default=LF.RUNS, help="cached plain-run records (json); generated if missing")
     ap.add_argument("--out", default=LF.WEIGHTS)
     args = ap.parse_args()
     counts = [int(c) for c in args.runs.split(",")]
@@ -99,7 +102,8 @@ def main():
                    loss_last=float(hist[-1]), val_loss=float(net.loss(X[is_val], T[is_val])),
                    val_tau_err_median=float(np.median(dtau[is_val])), val_tau_err_max=float(dtau[is_val].max()),
                    train_tau_err_median=float(np.median(dtau[~is_val])), data_seconds=t_data,
-                   train_seconds=t_train, lattices=[list(d) for d in LATTICES], runs_per_lattice=counts)
+                   train_seconds=t_train, lattices=[list(d) for d in LATTICES], runs_per_lattice=counts,
+                   degree=LF.DEGREE)
     net.save(args.out, **summary)
     print(json.dumps(summary), flush=True)
 

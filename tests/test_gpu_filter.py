@@ -96,6 +96,40 @@ def test_filtered_solve_matches_unfiltered_oracle(kind):
     s.close()
 
 
+@pytest.mark.parametrize("kind,precision", [("dense", "fp64"), ("dense", "mixed_reorth"), ("stencil", "fp64"),
+                                            ("stencil", "mixed_reorth")])
+def test_certified_filtered_solve_matches_oracle(kind, precision):
+    """The certifying phase on B = p(A) (degree 16): pairs accepted by A's true residual at x^H A x."""
+    nev, m, mwin, tol = 6, 24, 12, 1e-9
+    if kind == "dense":
+        A11, A12 = inputs.dense_jsym(100, 0)
+        mv = lambda x: jsym.dense_matvec(A11, A12, x)
+        n, kw = 200, dict(kind="dense", A11=A11, A12=A12)
+    else:
+        dims = (4, 4, 4, 4)
+        U, W, mv = _stencil(dims, 1)
+        n, kw = 6 * 256, dict(kind="stencil", dims=dims, m0=8.5, kappa=0.3, U=U, W=W)
+    ref = tj.trlan_jsym(mv, n, nev + 1, m, mwin, 1e-12)
+    probe = _solver(nev=nev, m=m, mwin=mwin, tol=tol, precision=precision, **kw)
+    lo, hi = probe.bounds(20)
+    probe.close()
+    a = lo - 0.02 * (hi - lo)
+    tau = flt.cut_to_tau(0.5 * (ref["evals"][nev - 1] + ref["evals"][nev]), a, hi)
+    g = flt.damped_step_coeffs(tau, 16)
+    s = _solver(nev=nev, m=m, mwin=mwin, tol=tol, precision=precision, filter_final_coeffs=g, filter_window=(a, hi),
+                **kw)
+    st = s.solve()
+    ev, X, res = s.pairs()
+    assert (np.abs(ev - ref["evals"][:nev]) / np.abs(ref["evals"][:nev])).max() < 1e-10
+    assert (np.diff(ev) > 0).all()                     # reported as eigenvalues of A, ascending
+    Xh = X.cpu().numpy()
+    for i in range(nev):
+        assert np.linalg.norm(mv(Xh[:, i]) - ev[i] * Xh[:, i]) < tol
+    assert np.abs(Xh.conj().T @ Xh - np.eye(nev)).max() < 1e-10
+    assert st["n_matvec"] % 16 == 0                     # 16 products of A per Lanczos step
+    s.close()
+
+
 def test_bounds_bracket_the_spectrum():
     A11, A12 = inputs.dense_jsym(150, 6)
     lam = np.linalg.eigvalsh(jsym.assemble_block_form(A11, A12))
