@@ -230,6 +230,62 @@ def stencil_apply_roofline(dims, reps=20, seed=4):
             "frac_of_hbm": round(gbs / hbm, 4), "hbm_peak_gbs": hbm, "peak_source": src}
 
 
+# ---------------------------------------------------------------- learned polynomial filter
+LEARNED_LATTICES = {"16x16x16x16": dict(dims=(16, 16, 16, 16), nev=50, m=120, mwin=60),
+                    "24x24x24x48": dict(dims=(24, 24, 24, 48), nev=100, m=200, mwin=100)}
+
+
+def learned_compare(B, torch, lattice, with_fp64=False, seed=1, m0=8.5, kappa=0.3):
+    """Time to nev pairs at residual 1e-8 on the seeded stencil (complex64 links, as the workload states):
+    the learned-filter form (jtrlan_bounds + network inference + JTRLAN_MIXED_REORTH on B = p(A), every
+    pair certified by A's true residual) against the same solver unfiltered and, optionally, plain FP64.
+    Operator upload excluded; CUDA-synchronised wall clock around the solve calls."""
+    from paper_2001_07428_gb300 import learned_filter as LF
+    from paper_2001_07428_gb300.solver import JTRLan
+    cfg = LEARNED_LATTICES[lattice]
+    dims, nev, m, mwin = cfg["dims"], cfg["nev"], cfg["m"], cfg["mwin"]
+    U, W = inputs.stencil_links(dims, seed)
+    U, W = U.astype(np.complex64), W.astype(np.complex64)
+    dev = "cuda:%d" % torch.cuda.current_device()
+    kw = dict(kind="stencil", dims=dims, m0=m0, kappa=kappa, U=U, W=W, nev=nev, m=m, mwin=mwin, tol=TOL,
+              links_dtype="c64", device=dev)
+    out = {"workload": f"stencil_{lattice}", "n": 6 * inputs.lattice_volume(dims), "nev": nev, "m": m, "mwin": mwin,
+           "tol": TOL, "links": "complex64"}
+    net = LF.FilterNet.load(device=dev)
+
+    def timed_solve(s):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = s.solve()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, st
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g, win, feat = LF.learned_filter(net, U, W, dims, m0, kappa, nev, device=dev)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    s = JTRLan(precision="mixed_reorth", filter_final_coeffs=g, filter_window=win, **kw)
+    t, st = timed_solve(s)
+    ev_l, _, res_l = s.pairs()
+    s.close()
+    out["learned"] = {"value": t_setup + t, "unit": "s", "filter_setup_s": t_setup, "solve_s": t,
+                      "degree": len(g) - 1, "window": list(win), "cut_tau": float(np.cos(np.pi * (1 - g[0]))),
+                      "n_matvec": st["n_matvec"], "n_resid_matvec": st["n_resid_matvec"],
+                      "n_restarts": st["n_restarts"], "max_residual": float(res_l.max())}
+    forms = [("mixed_reorth", "mixed_reorth")] + ([("fp64", "fp64")] if with_fp64 else [])
+    for name, prec in forms:
+        s = JTRLan(precision=prec, **kw)
+        t, st = timed_solve(s)
+        ev, _, res = s.pairs()
+        s.close()
+        out[name] = {"value": t, "unit": "s", "n_matvec": st["n_matvec"], "n_restarts": st["n_restarts"],
+                     "max_residual": float(res.max())}
+        out["learned"]["max_rel_eig_diff_vs_" + name] = float(np.max(np.abs(ev_l - ev) / np.abs(ev)))
+        out["learned"]["speedup_vs_" + name] = round(t / out["learned"]["value"], 3)
+    return out
+
+
 # ---------------------------------------------------------------- batched dense instances
 BATCH = dict(count=512, lo=64, hi=512, size_seed=2, seed0=1000, nev=8, m=24, mwin=12)
 
@@ -554,6 +610,8 @@ def run_gb300(args, rank, world, local_rank):
             "kernels": kernels,
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
     line["stencil_fp32"] = {k: stencil_apply_roofline(v) for k, v in STENCIL_LATTICES.items()}
+    if not args.no_learned:
+        line["learned_filter"] = learned_compare(B, torch, "16x16x16x16", with_fp64=False)
     if not args.no_batched:
         line["batched_dense"] = batched_dense(B, torch, stream, args.steps, args.warmup,
                                               cpu=world == 1 and not args.no_cpu_baseline)
@@ -580,6 +638,10 @@ def main():
     ap.add_argument("--stencil-only", default=None, choices=sorted(STENCIL_LATTICES),
                     help="only time the FP32 stencil matvec on this lattice (for profiling)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched dense instances")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-filter comparison at 16^4")
+    ap.add_argument("--learned-only", default=None, choices=sorted(LEARNED_LATTICES),
+                    help="only compare the learned-filter form with the unfiltered solver on this lattice")
+    ap.add_argument("--with-fp64", action="store_true", help="with --learned-only: also time plain FP64")
     ap.add_argument("--batched-only", action="store_true", help="only time the batched dense instances")
     ap.add_argument("--batched-oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -600,6 +662,12 @@ def main():
         return
     if args.stencil_only:
         print(json.dumps(stencil_apply_roofline(STENCIL_LATTICES[args.stencil_only])), flush=True)
+        return
+    if args.learned_only:
+        import torch
+        from paper_2001_07428_gb300 import binding as B
+        B.load()
+        print(json.dumps(learned_compare(B, torch, args.learned_only, with_fp64=args.with_fp64)), flush=True)
         return
     if args.batched_only:
         import torch
