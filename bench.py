@@ -290,10 +290,12 @@ def learned_compare(B, torch, lattice, with_fp64=False, seed=1, m0=8.5, kappa=0.
 BATCH = dict(count=512, lo=64, hi=512, size_seed=2, seed0=1000, nev=8, m=24, mwin=12)
 
 
-def batch_instances():
+def batch_instances(count=None):
     """512 dense Hermitian J-symmetric instances (A11 = (G+G^H)/2, A12 = (K-K^T)/2, complex Gaussian),
-    n uniform over the even numbers 64..512, seeded as the parity test seeds them."""
-    sizes = inputs.batched_dense_sizes(BATCH["count"], BATCH["lo"], BATCH["hi"], seed=BATCH["size_seed"])
+    n uniform over the even numbers 64..512, seeded as the parity test seeds them (a smaller count
+    takes the first instances of the same sequence, for profiling)."""
+    count = count or BATCH["count"]
+    sizes = inputs.batched_dense_sizes(count, BATCH["lo"], BATCH["hi"], seed=BATCH["size_seed"])
     return sizes, [inputs.dense_jsym(int(n) // 2, BATCH["seed0"] + i) for i, n in enumerate(sizes)]
 
 
@@ -310,35 +312,42 @@ def batched_oracle_sample(picks):
     return time.perf_counter() - t0
 
 
-def batched_dense(B, torch, stream, steps, warmup, cpu=True):
+def batched_dense(B, torch, stream, steps, warmup, cpu=True, count=None, shape=None, forms=("fp64", "mixed_reorth")):
     """The batch in one persistent launch per solve (CUDA-graph replay, autotuned launch shape), plain
     FP64 and the compensated-FP32 form; K timed solves each after W warm-up solves.  Inputs (408 MB of
     packed blocks) exceed L2.  Roofline: algorithmic matvec work (32 flop and 32 bytes per (row pair,
     column) of the packed blocks per product) over the solve time."""
     import ctypes
-    sizes, blocks = batch_instances()
+    sizes, blocks = batch_instances(count)
+    count = len(sizes)
     dev = torch.device("cuda", torch.cuda.current_device())
     h2 = (sizes // 2).astype(np.int64) ** 2
-    out = {"workload": "dense_batch_512_n64-512", "count": BATCH["count"], "n_range": [BATCH["lo"], BATCH["hi"]],
+    out = {"workload": f"dense_batch_{count}_n64-512", "count": count, "n_range": [BATCH["lo"], BATCH["hi"]],
            "nev": BATCH["nev"], "m": BATCH["m"], "mwin": BATCH["mwin"], "tol": TOL,
            "packed_bytes": int(2 * 16 * h2.sum())}
     Ad = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in blocks]
     ops = [B.dense_operator(2 * a.shape[0], a.data_ptr(), b.data_ptr()) for a, b in Ad]
     evs = {}
     hbm, hsrc = measured_peaks()
-    for name, prec in (("fp64", B.JTRLAN_FP64), ("mixed_reorth", B.JTRLAN_MIXED_REORTH)):
+    precs = {"fp64": B.JTRLAN_FP64, "mixed_reorth": B.JTRLAN_MIXED_REORTH}
+    for name in forms:
+        prec = precs[name]
         bt = B.jtrlan_batch_create(ops, B.params(BATCH["nev"], BATCH["m"], BATCH["mwin"], TOL, precision=prec),
                                    stream.cuda_stream)
-        tuned = B.jtrlan_batch_tune(bt)
+        if shape:
+            B.jtrlan_batch_set_shape(bt, shape[0], shape[1])
+            tuned = {"threads": shape[0], "ctas_per_sm": shape[1], "best_ms": None}
+        else:
+            tuned = B.jtrlan_batch_tune(bt)
         for _ in range(warmup):
             st = B.jtrlan_batch_solve(bt)
         ts = []
         for _ in range(steps):
             st = B.jtrlan_batch_solve(bt)
             ts.append(st["solve_ms"] * 1e-3)
-        ev = np.zeros((BATCH["count"], BATCH["nev"]))
+        ev = np.zeros((count, BATCH["nev"]))
         res = np.zeros_like(ev)
-        ist = np.zeros((BATCH["count"], B.BATCH_STATS), dtype=np.int32)
+        ist = np.zeros((count, B.BATCH_STATS), dtype=np.int32)
         B.jtrlan_batch_results(bt, ev.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p),
                                ist.ctypes.data_as(ctypes.c_void_p))
         B.jtrlan_batch_destroy(bt)
@@ -353,7 +362,7 @@ def batched_dense(B, torch, stream, steps, warmup, cpu=True):
         prods = (ist[:, 0] + ist[:, 3]).astype(np.int64)
         flop = float(32 * (prods * h2).sum())
         byts = float(2 * 16 * (prods * h2).sum())
-        e = {"value": t, "unit": "s", "instances_per_s": round(BATCH["count"] / t, 1), "n_ok": int(st["n_ok"]),
+        e = {"value": t, "unit": "s", "instances_per_s": round(count / t, 1), "n_ok": int(st["n_ok"]),
              "n_matvec": int(st["n_matvec"]), "n_resid_matvec": int(st["n_resid_matvec"]),
              "max_outer_iterations": int(st["max_restarts"]), "max_residual": float(res.max()),
              "grid": st["grid"], "threads": st["threads"], "tuned": tuned, "graph": st["graph"],
@@ -363,15 +372,18 @@ def batched_dense(B, torch, stream, steps, warmup, cpu=True):
         e["frac_of_fp64_peak"] = round(e["matvec_tflops"] / FP64_PEAK_TFLOPS, 4)
         e["frac_of_hbm"] = round(e["matvec_gbs"] / hbm, 4)
         out[name] = e
-    out["speedup_vs_fp64"] = round(out["fp64"]["value"] / out["mixed_reorth"]["value"], 3)
-    out["max_rel_eig_diff_vs_fp64"] = float(np.max(np.abs(evs["mixed_reorth"] - evs["fp64"]) / np.abs(evs["fp64"])))
+    if len(forms) == 2:
+        out["speedup_vs_fp64"] = round(out["fp64"]["value"] / out["mixed_reorth"]["value"], 3)
+        out["max_rel_eig_diff_vs_fp64"] = float(np.max(np.abs(evs["mixed_reorth"] - evs["fp64"]) / np.abs(evs["fp64"])))
     out["hbm_peak_gbs"], out["hbm_peak_source"] = hbm, hsrc
+    if count != BATCH["count"]:
+        return out
     # end to end: pinned host blocks -> create (H2D) -> solve -> eigenvalues and vectors to host
     Hh = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in blocks]
     ops_h = [B.dense_operator(2 * a.shape[0], a.data_ptr(), b.data_ptr()) for a, b in Hh]
     Xh = torch.empty(int(sizes.sum()) * BATCH["nev"], dtype=torch.complex128).pin_memory()
-    ev = np.zeros((BATCH["count"], BATCH["nev"]))
-    chosen = min(("fp64", "mixed_reorth"), key=lambda k: out[k]["value"])
+    ev = np.zeros((count, BATCH["nev"]))
+    chosen = min(forms, key=lambda k: out[k]["value"])
     prec = B.JTRLAN_FP64 if chosen == "fp64" else B.JTRLAN_MIXED_REORTH
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -643,6 +655,9 @@ def main():
                     help="only compare the learned-filter form with the unfiltered solver on this lattice")
     ap.add_argument("--with-fp64", action="store_true", help="with --learned-only: also time plain FP64")
     ap.add_argument("--batched-only", action="store_true", help="only time the batched dense instances")
+    ap.add_argument("--batch-count", type=int, default=None, help="with --batched-only: the first N instances")
+    ap.add_argument("--batch-shape", default=None, help="with --batched-only: THREADS,CTAS_PER_SM instead of tuning")
+    ap.add_argument("--batch-forms", default="fp64,mixed_reorth", help="with --batched-only: forms to time")
     ap.add_argument("--batched-oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-restarts", type=int, default=4, help=argparse.SUPPRESS)
@@ -673,8 +688,10 @@ def main():
         import torch
         from paper_2001_07428_gb300 import binding as B
         B.load()
+        shape = tuple(int(v) for v in args.batch_shape.split(",")) if args.batch_shape else None
         print(json.dumps(batched_dense(B, torch, torch.cuda.current_stream(), args.steps, args.warmup,
-                                       cpu=not args.no_cpu_baseline)), flush=True)
+                                       cpu=not args.no_cpu_baseline, count=args.batch_count, shape=shape,
+                                       forms=tuple(args.batch_forms.split(",")))), flush=True)
         return
     if world > 1:
         import torch
