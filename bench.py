@@ -286,6 +286,42 @@ def learned_compare(B, torch, lattice, with_fp64=False, seed=1, m0=8.5, kappa=0.
     return out
 
 
+# ---------------------------------------------------------------- J-TRLan vs plain TRLAN (Sec. 4, Case A)
+CASE_A_JSYM = [(5, 10, 50), (5, 10, 100), (5, 10, 150), (5, 10, 200),
+               (10, 20, 50), (10, 20, 100), (10, 20, 150), (10, 20, 200)]
+
+
+def case_a_sweep(B, torch, count=10, n=2000, tol=1e-13):
+    """The parameter sweep of the paper's Case A table on `count` regenerated matrices (inputs.case_a,
+    seeds 0..count-1): the largest nev pairs with TRLAN-JSYM at (nev, mwin, m) and with plain TRLAN
+    (W removed) at the doubled parameters, plain FP64, tol 1e-13.  Reports [min, mean, max] of the
+    outer iterations N_conv and of N_MV over the matrices, and the eigenvalue agreement with the
+    generator's Lambda."""
+    from paper_2001_07428_gb300.solver import JTRLan
+    mats = [inputs.case_a(n, seed) for seed in range(count)]
+    dev = "cuda:%d" % torch.cuda.current_device()
+    rows = []
+    for nev, mwin, m in CASE_A_JSYM:
+        for name, (q, w, mm, plain) in (("TRLAN-JSYM", (nev, mwin, m, False)), ("TRLAN", (2 * nev, 2 * mwin, 2 * m, True))):
+            nconv, nmv, err = [], [], 0.0
+            for A11, A12, lam in mats:
+                s = JTRLan(kind="dense", A11=A11, A12=A12, nev=q, m=mm, mwin=w, tol=tol, which="largest",
+                           precision="fp64", plain_trlan=plain, device=dev)
+                st = s.solve()
+                ev, _, _ = s.pairs()
+                s.close()
+                top = np.sort(lam)[::-1][:nev]
+                want = np.repeat(top, 2) if plain else top
+                err = max(err, float(np.abs(ev - want).max()))
+                nconv.append(st["n_restarts"])
+                nmv.append(st["n_matvec"])
+            rows.append({"algorithm": name, "nev": q, "mwin": w, "m": mm,
+                         "N_conv": [int(min(nconv)), round(float(np.mean(nconv)), 1), int(max(nconv))],
+                         "N_MV": [int(min(nmv)), round(float(np.mean(nmv)), 1), int(max(nmv))],
+                         "max_abs_eig_err": err})
+    return {"workload": f"case_a_n{n}_x{count}", "tol": tol, "which": "largest", "rows": rows}
+
+
 # ---------------------------------------------------------------- batched dense instances
 BATCH = dict(count=512, lo=64, hi=512, size_seed=2, seed0=1000, nev=8, m=24, mwin=12)
 
@@ -658,6 +694,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=None, help="with --batched-only: the first N instances")
     ap.add_argument("--batch-shape", default=None, help="with --batched-only: THREADS,CTAS_PER_SM instead of tuning")
     ap.add_argument("--batch-forms", default="fp64,mixed_reorth", help="with --batched-only: forms to time")
+    ap.add_argument("--case-a", action="store_true", help="only run the Case A sweep (TRLAN-JSYM vs plain TRLAN)")
     ap.add_argument("--batched-oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-restarts", type=int, default=4, help=argparse.SUPPRESS)
@@ -677,6 +714,12 @@ def main():
         return
     if args.stencil_only:
         print(json.dumps(stencil_apply_roofline(STENCIL_LATTICES[args.stencil_only])), flush=True)
+        return
+    if args.case_a:
+        import torch
+        from paper_2001_07428_gb300 import binding as B
+        B.load()
+        print(json.dumps(case_a_sweep(B, torch)), flush=True)
         return
     if args.learned_only:
         import torch

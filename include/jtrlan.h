@@ -131,6 +131,8 @@ typedef struct {
   double filter_lo, filter_hi;  /* the window [a, b] of the Chebyshev variable (A - c)/e */
   int filter_final_degree;      /* 0: none; else the degree of the certifying phase's filter */
   const double* filter_final_coeffs;  /* host, filter_final_degree + 1 coefficients (copied) */
+  int plain_trlan;    /* nonzero: the standard TRLAN the paper compares against (Algorithms 1 and 2
+                         with W removed: Gram-Schmidt against V only) */
 } jtrlan_params;
 
 /* Counters of the last solve (Sec. 3 counts only the Lanczos-step products as N_MV). */

@@ -36,11 +36,14 @@ class NoConvergenceError(RuntimeError):
 
 
 def lanczos_jsym(matvec, V, T, k, m, gamma=np.sqrt(2.0), gs_max_passes=3,
-                 breakdown_tol=1e-14, stats=None):
+                 breakdown_tol=1e-14, stats=None, use_w=True):
     """Algorithm 2: extend V[:, :k+1], T[:k+1, :k+1] to V[:, :m+1], T[:m+1, :m] (in place).
 
     ``T`` is the (m+1) x (m+1) real array holding T-bar; it is kept symmetric in its
     leading m x m part, and row m holds t_{m+1, m} = beta_m.
+
+    With use_w=False this is the Lanczos step of the standard TRLAN, which the paper obtains
+    by removing W from Algorithms 1 and 2 (Sec. 3).
     """
     for j in range(k, m):
         vj = V[:, j]
@@ -54,9 +57,10 @@ def lanczos_jsym(matvec, V, T, k, m, gamma=np.sqrt(2.0), gs_max_passes=3,
         b1 = b0
         for _ in range(gs_max_passes):                   # the reorthogonalisation loop (R4)
             for i in range(j + 1):
-                wi = pair(V[:, i])                       # w_i = J v_i^*
-                c = np.vdot(wi, y)
-                y = y - wi * c                           # orthogonalise against W_j
+                if use_w:
+                    wi = pair(V[:, i])                   # w_i = J v_i^*
+                    c = np.vdot(wi, y)
+                    y = y - wi * c                       # orthogonalise against W_j
                 vi = V[:, i]
                 c = np.vdot(vi, y)
                 y = y - vi * c                           # ... and against V_j
@@ -78,7 +82,7 @@ def lanczos_jsym(matvec, V, T, k, m, gamma=np.sqrt(2.0), gs_max_passes=3,
 
 
 def trlan_jsym(matvec, n, nev, m, mwin, tol, which="smallest", v1=None, max_restarts=1000,
-               gs_max_passes=3, on_lanczos=None):
+               gs_max_passes=3, on_lanczos=None, use_w=True):
     """Algorithm 1 (TRLAN-JSYM), normal mode.
 
     Returns a dict with ``evals`` (nev,), ``X`` (n, nev), ``res`` (nev,), and the
@@ -100,7 +104,7 @@ def trlan_jsym(matvec, n, nev, m, mwin, tol, which="smallest", v1=None, max_rest
     res_est = np.full(nev, np.inf)
     history = []
     for _ in range(max_restarts):
-        lanczos_jsym(matvec, V, T, k, m, gs_max_passes=gs_max_passes, stats=stats)
+        lanczos_jsym(matvec, V, T, k, m, gs_max_passes=gs_max_passes, stats=stats, use_w=use_w)
         stats["n_restarts"] += 1
         if on_lanczos is not None:
             on_lanczos(V, T, k, m)

@@ -45,7 +45,7 @@ class jtrlan_params(ctypes.Structure):
                 ("v1", ctypes.c_void_p), ("check_jsym", ctypes.c_int), ("profile", ctypes.c_int),
                 ("filter_degree", ctypes.c_int), ("filter_coeffs", ctypes.c_void_p), ("filter_lo", ctypes.c_double),
                 ("filter_hi", ctypes.c_double), ("filter_final_degree", ctypes.c_int),
-                ("filter_final_coeffs", ctypes.c_void_p)]
+                ("filter_final_coeffs", ctypes.c_void_p), ("plain_trlan", ctypes.c_int)]
 
 
 class jtrlan_stats(ctypes.Structure):
@@ -328,7 +328,7 @@ def dense_operator(n, a11_ptr, a12_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
 
 def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_restarts=0,
            gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0, filter_coeffs=None, filter_window=None,
-           filter_final_coeffs=None) -> jtrlan_params:
+           filter_final_coeffs=None, plain_trlan=0) -> jtrlan_params:
     """filter_coeffs / filter_final_coeffs: float64 arrays g_0..g_d (kept alive on the struct until
     create copies them); filter_window: (lo, hi)."""
     p = jtrlan_params()
@@ -338,6 +338,7 @@ def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_
     p.v1 = v1_ptr
     p.check_jsym = int(check_jsym)
     p.profile = int(profile)
+    p.plain_trlan = int(plain_trlan)
     if filter_coeffs is not None:
         import numpy as np
         g = np.ascontiguousarray(filter_coeffs, dtype=np.float64)

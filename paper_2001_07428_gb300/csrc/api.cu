@@ -579,6 +579,7 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
   a.V = ph.V; a.n = n; a.h = c->h; a.y = ph.y; a.part_dot = c->part_dot; a.part_nrm = c->part_nrm;
   a.coef = c->coef; a.st = c->st; a.T = c->T; a.ldt = ldt; a.m = m; a.nblk = c->gs_nblk;
   a.rows_per_block = c->gs_rpb;
+  a.no_w = c->prm.plain_trlan ? 1 : 0;
   const double mv_units = ph.op.kind == JTRLAN_STENCIL4D ? (double)ph.op.vol : (double)c->h * (double)c->h;
   ev.assign(nev, 0.0);
   res.assign(nev, INFINITY);
@@ -781,6 +782,7 @@ jtrlan_status bounds_impl(jtrlan_ctx* c, int steps, double* lo, double* hi) {
   a.V = ph.V; a.n = n; a.h = c->h; a.y = ph.y; a.part_dot = c->part_dot; a.part_nrm = c->part_nrm;
   a.coef = c->coef; a.st = c->st; a.T = c->T; a.ldt = ldt; a.m = c->m; a.nblk = c->gs_nblk;
   a.rows_per_block = c->gs_rpb;
+  a.no_w = c->prm.plain_trlan ? 1 : 0;
   if (fp32) JT_TRY(lanczos_steps<float>(c, ph, a, 0, steps, false));
   else JT_TRY(lanczos_steps<double>(c, ph, a, 0, steps, false));
   LAUNCH(K_RITZ, launch_ritz(c->T, ldt, steps, 0, steps, JTRLAN_SMALLEST, c->lam, c->Z, c->ritz_flags, s));

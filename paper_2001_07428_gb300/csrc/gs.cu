@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kRedThreads) gs_reduce_kernel(GSArgs a, int fi
     }
     s0 = block_sum(s0, sh); s1 = block_sum(s1, sh); s2 = block_sum(s2, sh); s3 = block_sum(s3, sh);
     if (threadIdx.x == 0) {
-      coef4 c; c.vr = s0; c.vi = s1; c.wr = s2; c.wi = s3;
+      coef4 c; c.vr = s0; c.vi = s1; c.wr = a.no_w ? 0.0 : s2; c.wi = a.no_w ? 0.0 : s3;
       a.coef[col] = c;
     }
   } else {

@@ -51,6 +51,7 @@ struct GSArgs {
   int ldt;             // m + 1
   int m;
   int nblk;            // blocks of the row-parallel GS kernels
+  int no_w;            // nonzero: plain TRLAN (Gram-Schmidt against V only, W removed)
   int rows_per_block;  // row pairs per block (multiple of 32)
 };
 int gs_blocks(int64_t h, int* rows_per_block);

@@ -86,6 +86,46 @@ def free_links(dims):
     return U, W
 
 
+def case_a(n: int, seed: int):
+    """A random Hermitian J-symmetric matrix in the diagonal block form A = U diag(L, L) U^H,
+    U = [[X1, -X2^*], [X2, X1^*]] (Sec. 4, Case A): L uniform in (0, 1); X1, X2 entries uniform in
+    the box (-1, 1) + i(-1, 1), then made to satisfy X1^H X1 + X2^H X2 = I and X1^T X2 - X2^T X1 = O
+    by Gram-Schmidt against the columns of X and of J X^* (two passes, in blocks of 50 columns).
+    Returns (A11, A12, L): the blocks of the block form (eq. (4)) and the n/2 eigenvalues."""
+    h = n // 2
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(0.0, 1.0, h)
+    X = rng.uniform(-1, 1, (n, h)) + 1j * rng.uniform(-1, 1, (n, h))
+
+    def jstar(Y):            # columns J y^* with J = [[O, -I], [I, O]]
+        return np.concatenate([-np.conj(Y[h:]), np.conj(Y[:h])], axis=0)
+
+    done = 0
+    while done < h:
+        b = min(50, h - done)
+        blk = X[:, done:done + b]
+        for _ in range(2):   # against the finished columns and their partners
+            if done:
+                Q = X[:, :done]
+                blk = blk - Q @ (Q.conj().T @ blk)
+                P = jstar(Q)
+                blk = blk - P @ (P.conj().T @ blk)
+        for c in range(b):   # within the block, column by column
+            x = blk[:, c]
+            for _ in range(2):
+                if c:
+                    Q = blk[:, :c]
+                    x = x - Q @ (Q.conj().T @ x)
+                    P = jstar(Q)
+                    x = x - P @ (P.conj().T @ x)
+            blk[:, c] = x / np.linalg.norm(x)
+        X[:, done:done + b] = blk
+        done += b
+    U = np.concatenate([X, jstar(X)], axis=1)
+    A = (U * np.concatenate([lam, lam])) @ U.conj().T
+    return np.ascontiguousarray(A[:h, :h]), np.ascontiguousarray(A[:h, h:]), lam
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return complex_gaussian(rng, (n,))

@@ -158,3 +158,28 @@ def test_batch_full_size_sampled(precision):
         assert (np.abs(ev[i] - bf) / np.abs(bf)).max() < 1e-10, (i, sizes[i])
         _check_vectors(A11, A12, ev[i], b.vectors(i), tol)
     b.close()
+
+
+# ----------------------------------------------------------------------------- plain TRLAN (W removed)
+@pytest.mark.parametrize("precision", ["fp64", "mixed_reorth"])
+def test_plain_trlan_matches_oracle_on_case_a(precision):
+    from paper_2001_07428_gb300.solver import JTRLan
+    A11, A12, lam = inputs.case_a(400, 3)
+    mv = lambda x: jsym.dense_matvec(A11, A12, x)
+    top = np.sort(lam)[::-1][:5]
+    s = JTRLan(kind="dense", A11=A11, A12=A12, nev=10, m=100, mwin=20, tol=1e-11, which="largest",
+               precision=precision, plain_trlan=True, device="cuda:0")
+    st = s.solve()
+    ev, X, res = s.pairs()
+    s.close()
+    assert np.abs(ev - np.repeat(top, 2)).max() < 1e-12
+    Xh = X.cpu().numpy()
+    assert np.abs(Xh.conj().T @ Xh - np.eye(10)).max() < 1e-10
+    for i in range(10):
+        assert np.linalg.norm(mv(Xh[:, i]) - ev[i] * Xh[:, i]) < 1e-11
+    ref = tj.trlan_jsym(mv, 400, 10, 100, 20, 1e-11, which="largest", use_w=False)
+    js = JTRLan(kind="dense", A11=A11, A12=A12, nev=5, m=50, mwin=10, tol=1e-11, which="largest",
+                precision=precision, device="cuda:0")
+    st_js = js.solve()
+    js.close()
+    assert st["n_matvec"] > 1.5 * st_js["n_matvec"] and abs(st["n_matvec"] - ref["n_matvec"]) <= 0.2 * ref["n_matvec"]
