@@ -269,7 +269,15 @@ def learned_compare(B, torch, lattice, with_fp64=False, seed=1, m0=8.5, kappa=0.
     t, st = timed_solve(s)
     ev_l, _, res_l = s.pairs()
     s.close()
-    out["learned"] = {"value": t_setup + t, "unit": "s", "filter_setup_s": t_setup, "solve_s": t,
+    # one more solve with the library's per-launch CUDA-event profile: where the learned form spends its time
+    sp = JTRLan(precision="mixed_reorth", filter_final_coeffs=g, filter_window=win, profile=True, **kw)
+    sp.solve()
+    prof = sp.profile()
+    sp.close()
+    tot = sum(v["ms"] for v in prof.values()) or 1.0
+    kernels = {k: {"ms": round(v["ms"], 2), "launches": v["launches"], "share": round(v["ms"] / tot, 4)}
+               for k, v in prof.items() if v["launches"]}
+    out["learned"] = {"value": t_setup + t, "unit": "s", "filter_setup_s": t_setup, "solve_s": t, "kernels": kernels,
                       "degree": len(g) - 1, "window": list(win), "cut_tau": float(np.cos(np.pi * (1 - g[0]))),
                       "n_matvec": st["n_matvec"], "n_resid_matvec": st["n_resid_matvec"],
                       "n_restarts": st["n_restarts"], "max_residual": float(res_l.max())}

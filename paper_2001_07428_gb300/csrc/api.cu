@@ -462,6 +462,19 @@ jtrlan_status filter_apply_cert(jtrlan_ctx* c, Phase& ph, int j) {
   const int64_t n = c->n;
   const int d = (int)ph.fcoef.size() - 1;
   const double* g = ph.fcoef.data();
+  if (ph.dfmv) {   // stencil: each recurrence step fused into the compensated-FP32 product (float-float)
+    void* acc = ph.fbuf[0];
+    void* B[2] = {ph.fbuf[1], ph.fbuf[2]};
+    const void* vj = col(ph.V, n, j, ph.cs);
+    const OpDev& o = ph.opdf;
+    LAUNCH(K_MATVEC, launch_matvec_df_cheb(o, vj, nullptr, B[1], acc, vj, ph.y, ph.alpha_part, o.kappa, o.m0, c->fc,
+                                           1.0 / c->fe, g[1], g[0], 1, d == 1, s));
+    for (int k = 2; k <= d; ++k)
+      LAUNCH(K_MATVEC, launch_matvec_df_cheb(o, B[(k - 1) & 1], k == 2 ? vj : B[k & 1], B[k & 1], acc, vj, ph.y,
+                                             ph.alpha_part, o.kappa, o.m0, c->fc, 2.0 / c->fe, g[k], 0.0, 0, k == d,
+                                             s));
+    return JTRLAN_OK;
+  }
   void* ax = ph.fbuf[0];
   void* B[2] = {ph.fbuf[1], ph.fbuf[2]};
   void* sp = ph.fbuf[3];
@@ -520,7 +533,8 @@ jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1,
   const int64_t n = c->n;
   const size_t cs = ph.cs;
   if (ph.df) LAUNCH(K_OTHER, launch_fp64_from_df(col(ph.V, n, j0, cs), ph.x, n, s));   // v_j0 in FP64
-  const int mv_parts = filtered ? cheb_blocks(n) : ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk;
+  const int mv_parts = (filtered && !(ph.certify && ph.dfmv)) ? cheb_blocks(n)
+                       : ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk;
   for (int j = j0; j < j1; ++j) {
     if (filtered) {
       if constexpr (std::is_same<R, float>::value)

@@ -465,6 +465,62 @@ __device__ __forceinline__ void cdf_accc(float* s, float* e, float4 a, float4 b)
 }
 __device__ __forceinline__ float4 cneg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
 
+// The hopping sums of site s, colour a, in compensated FP32: (ys1, ye1) and (ys2, ye2) for the U
+// terms of y1 and y2, (ws1, we1) and (ws2, we2) for the W terms (kappa not yet applied).
+struct DfSums {
+  float ys1[2], ye1[2], ys2[2], ye2[2], ws1[2], we1[2], ws2[2], we2[2];
+};
+
+__device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* __restrict__ x, int s, int a,
+                                                DfSums& r) {
+  const int vol = (int)op.vol;
+  const int64_t h = op.h;
+  const float4* U = (const float4*)op.U;
+  const float4* W = (const float4*)op.W;
+  const float4* x1 = x;
+  const float4* x2 = x + h;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    r.ys1[c] = r.ye1[c] = r.ys2[c] = r.ye2[c] = 0.f;
+    r.ws1[c] = r.we1[c] = r.ws2[c] = r.we2[c] = 0.f;
+  }
+  int coord[4];
+  {
+    int q = s;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) { coord[d] = q % op.dims[d]; q /= op.dims[d]; }
+    coord[3] = q;
+  }
+  int stride = 1;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int L = op.dims[mu];
+    const int c = coord[mu];
+    const int sp = (c == L - 1) ? s - (L - 1) * stride : s + stride;
+    const int sm = (c == 0) ? s + (L - 1) * stride : s - stride;
+    stride *= L;
+    const float4* Um = U + (int64_t)mu * 9 * vol;
+    const float4* Wm = W + (int64_t)mu * 9 * vol;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float4 p1 = x1[3 * sp + b], p2 = x2[3 * sp + b];
+      const float4 m1 = x1[3 * sm + b], m2 = x2[3 * sm + b];
+      const float4 uf = Um[(a * 3 + b) * vol + s];    // U(s)_{ab}
+      const float4 ub = Um[(b * 3 + a) * vol + sm];   // U(s-mu)_{ba}
+      const float4 wf = Wm[(a * 3 + b) * vol + s];    // W(s)_{ab}
+      const float4 wb = Wm[(b * 3 + a) * vol + sm];   // W(s-mu)_{ba}
+      cdf_acc(r.ys1, r.ye1, uf, p1);           // U(s) x1(s+mu)
+      cdf_accc(r.ys1, r.ye1, ub, m1);          // U(s-mu)^H x1(s-mu)
+      cdf_accc(r.ys2, r.ye2, uf, p2);          // U(s)^* x2(s+mu)
+      cdf_acc(r.ys2, r.ye2, ub, m2);           // U(s-mu)^T x2(s-mu)
+      cdf_acc(r.ws1, r.we1, wf, p2);           // W(s) x2(s+mu)
+      cdf_acc(r.ws1, r.we1, cneg(wb), m2);     // -W(s-mu)^T x2(s-mu)
+      cdf_accc(r.ws2, r.we2, cneg(wf), p1);    // -W(s)^* x1(s+mu)
+      cdf_accc(r.ws2, r.we2, wb, m1);          // +W(s-mu)^H x1(s-mu)
+    }
+  }
+}
+
 __global__ void __launch_bounds__(3 * kDfSites)
 stencil_df_kernel(OpDev op, const float4* __restrict__ x, double2* __restrict__ Y, double* __restrict__ part) {
   __shared__ double sh[32];
@@ -474,54 +530,15 @@ stencil_df_kernel(OpDev op, const float4* __restrict__ x, double2* __restrict__ 
   const int a = threadIdx.x / kDfSites;
   double c0 = 0.0, c1 = 0.0;
   if (s < vol) {
-    const float4* U = (const float4*)op.U;
-    const float4* W = (const float4*)op.W;
-    const float4* x1 = x;
-    const float4* x2 = x + h;
-    float ys1[2] = {0.f, 0.f}, ye1[2] = {0.f, 0.f}, ys2[2] = {0.f, 0.f}, ye2[2] = {0.f, 0.f};
-    float ws1[2] = {0.f, 0.f}, we1[2] = {0.f, 0.f}, ws2[2] = {0.f, 0.f}, we2[2] = {0.f, 0.f};
-    int coord[4];
-    {
-      int r = s;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) { coord[d] = r % op.dims[d]; r /= op.dims[d]; }
-      coord[3] = r;
-    }
-    int stride = 1;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      const int L = op.dims[mu];
-      const int c = coord[mu];
-      const int sp = (c == L - 1) ? s - (L - 1) * stride : s + stride;
-      const int sm = (c == 0) ? s + (L - 1) * stride : s - stride;
-      stride *= L;
-      const float4* Um = U + (int64_t)mu * 9 * vol;
-      const float4* Wm = W + (int64_t)mu * 9 * vol;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const float4 p1 = x1[3 * sp + b], p2 = x2[3 * sp + b];
-        const float4 m1 = x1[3 * sm + b], m2 = x2[3 * sm + b];
-        const float4 uf = Um[(a * 3 + b) * vol + s];    // U(s)_{ab}
-        const float4 ub = Um[(b * 3 + a) * vol + sm];   // U(s-mu)_{ba}
-        const float4 wf = Wm[(a * 3 + b) * vol + s];    // W(s)_{ab}
-        const float4 wb = Wm[(b * 3 + a) * vol + sm];   // W(s-mu)_{ba}
-        cdf_acc(ys1, ye1, uf, p1);           // U(s) x1(s+mu)
-        cdf_accc(ys1, ye1, ub, m1);          // U(s-mu)^H x1(s-mu)
-        cdf_accc(ys2, ye2, uf, p2);          // U(s)^* x2(s+mu)
-        cdf_acc(ys2, ye2, ub, m2);           // U(s-mu)^T x2(s-mu)
-        cdf_acc(ws1, we1, wf, p2);           // W(s) x2(s+mu)
-        cdf_acc(ws1, we1, cneg(wb), m2);     // -W(s-mu)^T x2(s-mu)
-        cdf_accc(ws2, we2, cneg(wf), p1);    // -W(s)^* x1(s+mu)
-        cdf_accc(ws2, we2, wb, m1);          // +W(s-mu)^H x1(s-mu)
-      }
-    }
+    DfSums r;
+    stencil_df_sums(op, x, s, a, r);
     const int64_t e1 = 3 * (int64_t)s + a;
-    const double2 xa = join(x1[e1]), xb = join(x2[e1]);
+    const double2 xa = join(x[e1]), xb = join(x[h + e1]);
     const double kap = op.kappa, m0 = op.m0;
-    const double2 o1 = make_double2((double)ys1[0] + (double)ye1[0] + kap * ((double)ws1[0] + (double)we1[0]) + m0 * xa.x,
-                                    (double)ys1[1] + (double)ye1[1] + kap * ((double)ws1[1] + (double)we1[1]) + m0 * xa.y);
-    const double2 o2 = make_double2((double)ys2[0] + (double)ye2[0] + kap * ((double)ws2[0] + (double)we2[0]) + m0 * xb.x,
-                                    (double)ys2[1] + (double)ye2[1] + kap * ((double)ws2[1] + (double)we2[1]) + m0 * xb.y);
+    const double2 o1 = make_double2((double)r.ys1[0] + (double)r.ye1[0] + kap * ((double)r.ws1[0] + (double)r.we1[0]) + m0 * xa.x,
+                                    (double)r.ys1[1] + (double)r.ye1[1] + kap * ((double)r.ws1[1] + (double)r.we1[1]) + m0 * xa.y);
+    const double2 o2 = make_double2((double)r.ys2[0] + (double)r.ye2[0] + kap * ((double)r.ws2[0] + (double)r.we2[0]) + m0 * xb.x,
+                                    (double)r.ys2[1] + (double)r.ye2[1] + kap * ((double)r.ws2[1] + (double)r.we2[1]) + m0 * xb.y);
     Y[e1] = o1;
     Y[h + e1] = o2;
     if (part) {
@@ -530,6 +547,105 @@ stencil_df_kernel(OpDev op, const float4* __restrict__ x, double2* __restrict__ 
     }
   }
   if (part) {
+    c0 = block_sum(c0, sh);
+    c1 = block_sum(c1, sh);
+    if (threadIdx.x == 0) ((double2*)part)[blockIdx.x] = make_double2(c0, c1);
+  }
+}
+
+// ------------------------------------------------------------------ float-float scalars
+// hi + lo with |lo| <= ulp(hi)/2; the operations below keep about 48 significant bits.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_norm(float s, float e) {   // two_sum renormalisation
+  ff r;
+  two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return ff_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {   // exact split of hi * hi plus first-order cross terms
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  ff r;
+  r.hi = __fadd_rn(p, e);                                   // fast two-sum: |p| >= |e|
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, p));
+  return r;
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_re(float4 v) { return ff{v.x, v.z}; }
+__device__ __forceinline__ ff ff_im(float4 v) { return ff{v.y, v.w}; }
+
+// Constants of one Chebyshev step as float-float pairs.
+struct ChebConsts {
+  ff kappa, m0, c, sc, g, g0;
+};
+
+// One step of the Chebyshev recurrence for B = p(A) fused into the compensated-FP32 product t -> A t
+// (x = t_k, the current recurrence vector, as (hi, lo)):
+//   t_next = sc (A t - c t) - t_prev     (t_prev omitted when null)
+//   acc    = g0 v + g t_next (init)   or   acc += g t_next
+// all in float-float arithmetic on the FP32 pipe; t_next and acc are stored as (hi, lo) float4, so
+// t_next feeds the next product directly.  On the last step acc goes out in FP64 to y, with the
+// per-block partials of conj(v) y (the alpha of Algorithm 2).  t_next may alias t_prev (the same
+// thread reads an entry before writing it); neighbours are read from x only.
+__global__ void __launch_bounds__(3 * kDfSites)
+stencil_df_cheb_kernel(OpDev op, const float4* __restrict__ x, const float4* t_prev, float4* t_next,
+                       float4* __restrict__ acc, const float4* __restrict__ v, double2* __restrict__ y,
+                       double* __restrict__ part, ChebConsts k, int init, int last) {
+  __shared__ double sh[32];
+  const int vol = (int)op.vol;
+  const int64_t h = op.h;
+  const int s = blockIdx.x * kDfSites + (threadIdx.x % kDfSites);
+  const int a = threadIdx.x / kDfSites;
+  double c0 = 0.0, c1 = 0.0;
+  if (s < vol) {
+    DfSums r;
+    stencil_df_sums(op, x, s, a, r);
+    const int64_t e1 = 3 * (int64_t)s + a;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int64_t e = e1 + (half ? h : 0);
+      const float* ys = half ? r.ys2 : r.ys1;
+      const float* ye = half ? r.ye2 : r.ye1;
+      const float* ws = half ? r.ws2 : r.ws1;
+      const float* we = half ? r.we2 : r.we1;
+      const float4 xt = x[e];
+      const float4 tp = t_prev ? t_prev[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 ac = init ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[e];
+      const float4 vv = (init || last) ? v[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      ff nx[2], an[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const ff xc = c ? ff_im(xt) : ff_re(xt);
+        // (A t)_c = U sums + kappa W sums + m0 t
+        ff u = ff_add(ff_norm(ys[c], ye[c]), ff_mul(k.kappa, ff_norm(ws[c], we[c])));
+        u = ff_add(u, ff_mul(k.m0, xc));
+        ff d = ff_mul(k.sc, ff_add(u, ff_neg(ff_mul(k.c, xc))));
+        if (t_prev) d = ff_add(d, ff_neg(c ? ff_im(tp) : ff_re(tp)));
+        nx[c] = d;
+        const ff gn = ff_mul(k.g, d);
+        an[c] = init ? ff_add(ff_mul(k.g0, c ? ff_im(vv) : ff_re(vv)), gn) : ff_add(c ? ff_im(ac) : ff_re(ac), gn);
+      }
+      t_next[e] = make_float4(nx[0].hi, nx[1].hi, nx[0].lo, nx[1].lo);
+      if (last) {
+        const double2 o = make_double2((double)an[0].hi + (double)an[0].lo, (double)an[1].hi + (double)an[1].lo);
+        y[e] = o;
+        const double2 vd = join(vv);
+        c0 += vd.x * o.x + vd.y * o.y;
+        c1 += vd.x * o.y - vd.y * o.x;
+      } else {
+        acc[e] = make_float4(an[0].hi, an[1].hi, an[0].lo, an[1].lo);
+      }
+    }
+  }
+  if (last) {
     c0 = block_sum(c0, sh);
     c1 = block_sum(c1, sh);
     if (threadIdx.x == 0) ((double2*)part)[blockIdx.x] = make_double2(c0, c1);
@@ -610,6 +726,17 @@ int matvec_df_blocks(const OpDev& op) { return (int)((op.vol + kDfSites - 1) / k
 
 cudaError_t launch_matvec_df(const OpDev& op, const void* x, void* y, double* part, cudaStream_t s) {
   stencil_df_kernel<<<matvec_df_blocks(op), 3 * kDfSites, 0, s>>>(op, (const float4*)x, (double2*)y, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_df_cheb(const OpDev& op, const void* x, const void* t_prev, void* t_next, void* acc,
+                                  const void* v, void* y, double* part, double kappa, double m0, double c, double sc,
+                                  double g, double g0, int init, int last, cudaStream_t s) {
+  auto f = [](double d) { const float hi = (float)d; return ff{hi, (float)(d - (double)hi)}; };
+  ChebConsts k{f(kappa), f(m0), f(c), f(sc), f(g), f(g0)};
+  stencil_df_cheb_kernel<<<matvec_df_blocks(op), 3 * kDfSites, 0, s>>>(
+      op, (const float4*)x, (const float4*)t_prev, (float4*)t_next, (float4*)acc, (const float4*)v, (double2*)y,
+      part, k, init, last);
   return cudaGetLastError();
 }
 

@@ -86,6 +86,13 @@ cudaError_t launch_rotate_df(const void* V, int64_t n, int m, const double* Z, i
 // block partials of x^H y.  op.U / op.W: (hi, lo) links, structure-of-arrays [4][9][V].
 int matvec_df_blocks(const OpDev& op);
 cudaError_t launch_matvec_df(const OpDev& op, const void* x, void* y, double* part, cudaStream_t s);
+// One Chebyshev step of B = p(A) fused into the compensated-FP32 stencil product (x, t_prev, t_next,
+// acc, v: (hi, lo) float4 vectors; t_next may alias t_prev): t_next = sc (A x - c x) - t_prev,
+// acc = g0 v + g t_next (init) or acc += g t_next; on the last step acc goes to y (FP64) with
+// matvec_df_blocks(op) double2 partials of conj(v) y in part.
+cudaError_t launch_matvec_df_cheb(const OpDev& op, const void* x, const void* t_prev, void* t_next, void* acc,
+                                  const void* v, void* y, double* part, double kappa, double m0, double c, double sc,
+                                  double g, double g0, int init, int last, cudaStream_t s);
 cudaError_t launch_links_df(const void* in, void* out, int64_t vol, cudaStream_t s);
 
 // Kernel classes for the optional per-kernel profile.
