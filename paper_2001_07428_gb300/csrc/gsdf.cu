@@ -450,6 +450,7 @@ rotate_df_kernel(const float4* __restrict__ V, int64_t n, int m, const double* _
 // has FP64-level accuracy while the arithmetic runs on the FP32 pipes.  With `part` non-null the
 // block partials of x^H y (FP64) are written for alpha.
 constexpr int kDfSites = 64;
+constexpr int kDfMinBlocks = 4;   // 4 x 192 threads per SM (measured best of 2..6 at 16^4)
 
 __device__ __forceinline__ void cdf_acc(float* s, float* e, float4 a, float4 b) {   // (re, im) += a * b
   df_acc(s[0], e[0], a.x, a.z, b.x, b.z);
@@ -484,18 +485,15 @@ __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* _
     r.ys1[c] = r.ye1[c] = r.ys2[c] = r.ye2[c] = 0.f;
     r.ws1[c] = r.we1[c] = r.ws2[c] = r.we2[c] = 0.f;
   }
-  int coord[4];
-  {
-    int q = s;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) { coord[d] = q % op.dims[d]; q /= op.dims[d]; }
-    coord[3] = q;
-  }
+  const int d0 = op.dims[0], d1 = op.dims[1], d2 = op.dims[2], d3 = op.dims[3];
   int stride = 1;
-#pragma unroll
+  // the direction loop stays rolled: unrolled, its 4 x 3 x 8 compensated products overflowed the
+  // instruction cache (ncu: "no instruction" stalls as frequent as memory stalls); extents and
+  // coordinates are selected in registers, not indexed
+#pragma unroll 1
   for (int mu = 0; mu < 4; ++mu) {
-    const int L = op.dims[mu];
-    const int c = coord[mu];
+    const int L = mu == 0 ? d0 : mu == 1 ? d1 : mu == 2 ? d2 : d3;
+    const int c = (s / stride) % L;
     const int sp = (c == L - 1) ? s - (L - 1) * stride : s + stride;
     const int sm = (c == 0) ? s + (L - 1) * stride : s - stride;
     stride *= L;
@@ -521,7 +519,7 @@ __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* _
   }
 }
 
-__global__ void __launch_bounds__(3 * kDfSites)
+__global__ void __launch_bounds__(3 * kDfSites, kDfMinBlocks)
 stencil_df_kernel(OpDev op, const float4* __restrict__ x, double2* __restrict__ Y, double* __restrict__ part) {
   __shared__ double sh[32];
   const int vol = (int)op.vol;
@@ -595,7 +593,7 @@ struct ChebConsts {
 // t_next feeds the next product directly.  On the last step acc goes out in FP64 to y, with the
 // per-block partials of conj(v) y (the alpha of Algorithm 2).  t_next may alias t_prev (the same
 // thread reads an entry before writing it); neighbours are read from x only.
-__global__ void __launch_bounds__(3 * kDfSites)
+__global__ void __launch_bounds__(3 * kDfSites, kDfMinBlocks)
 stencil_df_cheb_kernel(OpDev op, const float4* __restrict__ x, const float4* t_prev, float4* t_next,
                        float4* __restrict__ acc, const float4* __restrict__ v, double2* __restrict__ y,
                        double* __restrict__ part, ChebConsts k, int init, int last) {
