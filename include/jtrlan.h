@@ -238,7 +238,8 @@ jtrlan_status jtrlan_damped_step(const double* tau, int count, int degree, float
  *     dimension ldx >= n.  lambda: host, ncols doubles.  res: host, ncols doubles (written).
  *   cuda_stream: the stream to run on (NULL = legacy default); the call synchronises it.
  * Limits: ncols <= JTRLAN_NOALLOC_MAX_COLS and ncols * B <= JTRLAN_NOALLOC_MAX_PARTIALS, where B is
- *   the number of blocks of one product (stencil: ceil(24 V / 256); dense: ceil((n/2) / 8)).
+ *   the number of blocks of one product (stencil: ceil(64 ceil(3 V / 8) / 256), which is
+ *   ceil(24 V / 256) when V is a multiple of 8; dense: ceil((n/2) / 8)).
  *   Larger requests fail with JTRLAN_EINVAL and a message naming the limit: split the columns.
  * The first call on a device looks up the array's device address there (cudaGetSymbolAddress with
  * that device current); make that first call before any stream capture on the device.

@@ -32,30 +32,35 @@ constexpr double kSqrt2 = 1.4142135623730951;
 // 8 x 4 real sums of its rows, then the warp transposes the 32 accumulators through shared memory
 // so that lane k adds up accumulator k: 31 adds per 32 results instead of 5-step shuffle trees
 // per result (on this GPU one FP64 warp instruction holds the FP64 pipe for ~16 cycles).
-constexpr int kDotCols = 8;
+// FP64 takes 4 columns per chunk (16 accumulators: about 80 registers, 3 blocks of 256 threads per
+// SM, so the usual grid runs in one wave); FP32 keeps 8.
+template <typename P>
+__host__ __device__ constexpr int dot_cols() { return sizeof(P) == 8 ? 4 : 8; }
 
 // R: storage type of V and y; P: arithmetic type of the projections (P = float on FP64 data is the
 // mixed form's FP32 inner product).
 template <typename R, typename P = R>
-__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1, P* red /* [8 warps][32][33] */) {
+__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1, P* red /* [8 warps][4 dot_cols][33] */) {
   using C = cplx<R>;
   using Q = cplx<P>;
   const C* V = (const C*)a.V;
   const C* y = (const C*)a.y;
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   const int64_t n = a.n, h = a.h;
-  P* wred = red + (size_t)q * 32 * 33;
+  constexpr int NC = dot_cols<P>();
+  constexpr int NA = 4 * NC;                     // accumulators per lane (32 or 16)
+  P* wred = red + (size_t)q * NA * 33;
   double* out = a.part_dot;
-  for (int c0 = kDotCols * q; c0 <= a.j; c0 += kDotCols * kColGroups) {
-    P acc[kDotCols][4];
+  for (int c0 = NC * q; c0 <= a.j; c0 += NC * kColGroups) {
+    P acc[NC][4];
 #pragma unroll
-    for (int c = 0; c < kDotCols; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = (P)0;
-    const int ncol = min(kDotCols, a.j + 1 - c0);
+    for (int c = 0; c < NC; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = (P)0;
+    const int ncol = min(NC, a.j + 1 - c0);
     for (int64_t p = p0 + lane; p < p1; p += 32) {
       const C yy1 = y[p], yy2 = y[h + p];
       const Q y1 = mk<P>((P)yy1.x, (P)yy1.y), y2 = mk<P>((P)yy2.x, (P)yy2.y);
 #pragma unroll
-      for (int c = 0; c < kDotCols; ++c) {
+      for (int c = 0; c < NC; ++c) {
         if (c < ncol) {
           const C* vi = V + (int64_t)(c0 + c) * n;
           const C vv1 = vi[p], vv2 = vi[h + p];
@@ -69,22 +74,26 @@ __device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1
       }
     }
 #pragma unroll
-    for (int c = 0; c < kDotCols; ++c)
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int t = 0; t < 4; ++t) wred[(4 * c + t) * 33 + lane] = acc[c][t];
     __syncwarp();
+    // accumulator row = lane % NA; 32 / NA lanes share a row, each adding NA of its 32 entries
+    const int row = lane % NA, part = lane / NA;
     P sum = (P)0;
 #pragma unroll 8
-    for (int l = 0; l < 32; ++l) sum += wred[lane * 33 + l];
+    for (int l = 0; l < NA; ++l) sum += wred[row * 33 + part * NA + l];
+#pragma unroll
+    for (int o = NA; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     __syncwarp();
-    const int c = lane >> 2, t = lane & 3;
-    if (c < ncol) out[((int64_t)(c0 + c) * a.nblk + blockIdx.x) * 4 + t] = (double)sum;
+    const int c = row >> 2, t = row & 3;
+    if (lane < NA && c < ncol) out[((int64_t)(c0 + c) * a.nblk + blockIdx.x) * 4 + t] = (double)sum;
   }
 }
 
 // First pass: alpha from the matvec partials, y -= alpha v_j, b0 partials, then the dot products.
 template <typename R, typename P = R>
-__global__ void __launch_bounds__(kGsThreads)
+__global__ void __launch_bounds__(kGsThreads, 3)
 gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_part) {
   using C = cplx<R>;
   __shared__ double sh[32];
@@ -131,7 +140,7 @@ gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_pa
 
 // Later passes: first finish the test of the previous pass, then the dot products.
 template <typename R>
-__global__ void __launch_bounds__(kGsThreads) gs_dot_kernel(GSArgs a, int pass) {
+__global__ void __launch_bounds__(kGsThreads, 3) gs_dot_kernel(GSArgs a, int pass) {
   __shared__ double sh[32];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ int s_skip;
@@ -374,7 +383,7 @@ int gs_blocks(int64_t h, int* rows_per_block) {
 }
 
 template <typename P>
-constexpr size_t dot_smem() { return (size_t)kColGroups * 32 * 33 * sizeof(P); }
+constexpr size_t dot_smem() { return (size_t)kColGroups * 4 * dot_cols<P>() * 33 * sizeof(P); }
 
 template <typename R>
 cudaError_t launch_gs_first(const GSArgs& a, const double2* alpha_part, int n_alpha_part, cudaStream_t s) {

@@ -33,19 +33,22 @@ stencil_kernel(OpDev op, const cplx<R>* __restrict__ X, cplx<R>* __restrict__ Y,
   const int64_t t = (int64_t)blockIdx.x * kMvThreads + threadIdx.x;
   const int col = blockIdx.y;
   const C* x = X + (MODE == MV_RESID ? (int64_t)cand[col] * ldx : 0);
-  const bool active = t < 24 * vol;
-  const int mu = (int)(t & 3);
-  int64_t r = t >> 2;
-  const int a = (int)(r % 3);
-  r /= 3;
-  const int half = (int)(r & 1);
-  const int64_t s = r >> 1;
+  // warp w takes half = w & 1 of the 8 (site, colour) items (w >> 1) * 8 + lane / 4, one direction
+  // per lane: the half is warp-uniform, so the two halves' code paths never diverge inside a warp
+  const int lane = (int)(t & 31);
+  const int64_t w = t >> 5;
+  const int mu = lane & 3;
+  const int half = (int)(w & 1);
+  const int64_t item = (w >> 1) * 8 + (lane >> 2);   // 3 s + a
+  const int a = (int)(item % 3);
+  const int64_t s = item / 3;
+  const bool active = item < 3 * vol;
 
   C accU = mk<R>(0, 0), accW = mk<R>(0, 0);
   if (active) {
-    int64_t stride = 1;
-    for (int d = 0; d < mu; ++d) stride *= op.dims[d];
-    const int L = op.dims[mu];
+    const int d0 = op.dims[0], d1 = op.dims[1], d2 = op.dims[2], d3 = op.dims[3];
+    const int64_t stride = mu == 0 ? 1 : mu == 1 ? (int64_t)d0 : mu == 2 ? (int64_t)d0 * d1 : (int64_t)d0 * d1 * d2;
+    const int L = mu == 0 ? d0 : mu == 1 ? d1 : mu == 2 ? d2 : d3;
     const int c = (int)((s / stride) % L);
     const int64_t sp = (c == L - 1) ? s - (int64_t)(L - 1) * stride : s + stride;
     const int64_t sm = (c == 0) ? s + (int64_t)(L - 1) * stride : s - stride;
@@ -294,7 +297,7 @@ cudaError_t launch_mode(const OpDev& op, const cplx<R>* x, cplx<R>* y, double* p
 int matvec_blocks(const OpDev& op) {
   if (op.kind == JTRLAN_STENCIL4D) {
     if (op.fp32) return (int)((op.vol + kSitesPerBlock - 1) / kSitesPerBlock);
-    return (int)((24 * op.vol + kMvThreads - 1) / kMvThreads);
+    return (int)((64 * ((3 * op.vol + 7) / 8) + kMvThreads - 1) / kMvThreads);   // 2 warps per 8 items
   }
   return (int)((op.h + kDenseRowsPerBlock - 1) / kDenseRowsPerBlock);
 }
