@@ -44,9 +44,9 @@ L2_FLUSH_BYTES = 512 << 20
 #     complex128 basis entries read = 32 B.
 #   rotate: per real multiply-add 2 flop; bytes negligible per unit (V read once, counted apart).
 FLOP_PER_UNIT = {"matvec": 2304.0, "resid": 2304.0, "gs_first": 32.0, "gs_dot": 32.0, "gs_update": 32.0,
-                 "rotate": 1.0}
+                 "gs_step": 32.0, "rotate": 1.0}
 BYTES_PER_UNIT = {"matvec": 84 * 16.0, "resid": 84 * 16.0, "gs_first": 32.0, "gs_dot": 32.0,
-                  "gs_update": 32.0}
+                  "gs_update": 32.0, "gs_step": 32.0}
 
 
 def log(*a):
@@ -662,6 +662,7 @@ def run_gb300(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args.workload, w),
             "solve_stats": {k: stats[-1][k] for k in ("n_matvec", "n_resid_matvec", "n_gs_passes", "n_restarts",
                                                        "icnv", "n_ritz_fallbacks")},
+            "step_ms": [round(x * 1e3, 3) for x in times],
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "mixed": mixed, "stencil_matvec": stencil,
             "kernels": kernels,
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}

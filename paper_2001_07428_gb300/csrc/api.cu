@@ -45,7 +45,7 @@ __global__ void c64_to_c128_kernel(const float2* in, double2* out, int64_t count
 }
 
 const char* kTagNames[K_NTAGS] = {"matvec", "gs_first", "gs_reduce", "gs_update", "gs_dot", "gs_normalize",
-                                  "ritz", "rotate", "resid", "shrink", "other", "ritz_fallback", "filter"};
+                                  "ritz", "rotate", "resid", "shrink", "other", "ritz_fallback", "filter", "gs_step"};
 
 // Optional per-launch CUDA-event timing, harvested at the host synchronisation points.
 struct Profiler {
@@ -151,6 +151,7 @@ struct jtrlan_ctx {
   int* h_order = nullptr;
   double* h_misc = nullptr;
   int gs_nblk = 0, gs_rpb = 0;
+  int coop64 = 0, coop32 = 0;      // grids of the cooperative Gram-Schmidt step (0: multi-kernel path)
   double fc = 0.0, fe = 1.0;       // filter window centre and half-width
   Profiler prof;
   double work_base[3] = {};        // device work counters carried across solve phases
@@ -374,13 +375,15 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
     JT_TRY(c->dalloc(&ph.alpha_part, (size_t)nb * sizeof(double2)));
     JT_TRY(c->dalloc(&ph.resid_part, (size_t)std::max(nb, ph.mv_nblk * c->nev) * sizeof(double)));
   }
+  if (!c->mixed) JT_CUDA(gs_coop_grid<double>(m, c->gs_nblk, &c->coop64));
+  if (prm->precision == JTRLAN_MIXED) JT_CUDA(gs_coop_grid<float>(m, c->gs_nblk, &c->coop32));
   JT_TRY(c->dalloc(&c->T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
   JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));
   JT_TRY(c->dalloc(&c->Z, (size_t)m * m * sizeof(double)));
   JT_TRY(c->dalloc(&c->ritz_ws, (size_t)2 * mp * mp * sizeof(double)));
   JT_TRY(c->dalloc(&c->ritz_flags, (size_t)(m + 1) * sizeof(int)));
   JT_TRY(c->dalloc(&c->part_dot, (size_t)(m + 1) * c->gs_nblk * sizeof(coef4)));
-  JT_TRY(c->dalloc(&c->part_nrm, (size_t)c->gs_nblk * sizeof(double)));
+  JT_TRY(c->dalloc(&c->part_nrm, (size_t)2 * c->gs_nblk * sizeof(double)));   // two slots (cooperative step)
   JT_TRY(c->dalloc(&c->coef, (size_t)(m + 1) * sizeof(coef4)));
   JT_TRY(c->dalloc(&c->st, sizeof(StepState)));
   JT_TRY(c->dalloc(&c->d_res, (size_t)c->nev * sizeof(double)));
@@ -561,6 +564,12 @@ jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1,
       }
       LAUNCH(K_GS_NORMALIZE, launch_gsdf_normalize(a, ph.x, s));
     } else {
+      const int coop = std::is_same<R, float>::value ? c->coop32 : c->coop64;
+      if (coop > 0) {   // the whole step in one cooperative launch
+        LAUNCH(K_GS_STEP, launch_gs_step_coop<R>(a, (const double2*)ph.alpha_part, mv_parts, c->gs_passes,
+                                                  c->part_nrm, coop, s));
+        continue;
+      }
       LAUNCH(K_GS_FIRST, launch_gs_first<R>(a, (const double2*)ph.alpha_part, mv_parts, s));
       LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
       LAUNCH(K_GS_UPDATE, launch_gs_update<R>(a, s));
@@ -639,6 +648,7 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     c->work[K_GS_FIRST] = c->work_base[0] + c->h_rep[2 * m + 4];
     c->work[K_GS_DOT] = c->work_base[1] + c->h_rep[2 * m + 5];
     c->work[K_GS_UPDATE] = c->work_base[2] + c->h_rep[2 * m + 6];
+    c->work[K_GS_STEP] = c->work[K_GS_FIRST] + c->work[K_GS_DOT] + c->work[K_GS_UPDATE];
     stt.n_ritz_fallbacks = c->fallback_base + (int)c->h_rep[2 * m + 7];
     if (c->h_rep[2 * m + 1] != 0.0) return fail(JTRLAN_EBREAKDOWN, "Lanczos breakdown: beta below 1e-14 max|T|");
     const double tmax = c->h_rep[2 * m + 3];

@@ -16,6 +16,8 @@
 // The data-dependent repeat runs without host synchronisation: every pass is launched, and each
 // kernel of a pass returns at once when the device-side flag st->done says the loop has exited.
 // All reductions use a fixed order, so results are reproducible run to run.
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace jtr {
@@ -36,11 +38,15 @@ constexpr double kSqrt2 = 1.4142135623730951;
 // SM, so the usual grid runs in one wave); FP32 keeps 8.
 template <typename P>
 __host__ __device__ constexpr int dot_cols() { return sizeof(P) == 8 ? 4 : 8; }
+// shared memory of the dot kernels' transposed reduction: [8 warps][4 dot_cols][33]
+template <typename P>
+__host__ __device__ constexpr size_t dot_smem() { return (size_t)kColGroups * 4 * dot_cols<P>() * 33 * sizeof(P); }
 
 // R: storage type of V and y; P: arithmetic type of the projections (P = float on FP64 data is the
 // mixed form's FP32 inner product).
 template <typename R, typename P = R>
-__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1, P* red /* [8 warps][4 dot_cols][33] */) {
+__device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1, P* red /* [8 warps][4 dot_cols][33] */,
+                                         int rb) {
   using C = cplx<R>;
   using Q = cplx<P>;
   const C* V = (const C*)a.V;
@@ -87,7 +93,7 @@ __device__ __forceinline__ void dot_body(const GSArgs& a, int64_t p0, int64_t p1
     for (int o = NA; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     __syncwarp();
     const int c = row >> 2, t = row & 3;
-    if (lane < NA && c < ncol) out[((int64_t)(c0 + c) * a.nblk + blockIdx.x) * 4 + t] = (double)sum;
+    if (lane < NA && c < ncol) out[((int64_t)(c0 + c) * a.nblk + rb) * 4 + t] = (double)sum;
   }
 }
 
@@ -135,7 +141,7 @@ gs_first_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_pa
   }
   const double nrm = block_sum((double)nrm_r, sh);  // its barriers also publish the y writes to the whole block
   if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
-  dot_body<R, P>(a, p0, p1, (P*)dyn_smem);
+  dot_body<R, P>(a, p0, p1, (P*)dyn_smem, blockIdx.x);
 }
 
 // Later passes: first finish the test of the previous pass, then the dot products.
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_dot_kernel(GSArgs a, int pas
   }
   const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
   const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, a.h);
-  dot_body<R>(a, p0, p1, (R*)dyn_smem);
+  dot_body<R>(a, p0, p1, (R*)dyn_smem, blockIdx.x);
 }
 
 // Reduce the dot partials of every column (one block per column); with `first`, block j+1 also
@@ -372,6 +378,191 @@ __global__ void jsym_check_kernel(const cplx<R>* v, const cplx<R>* y, int64_t h,
 
 }  // namespace
 
+// ------------------------------------------------------------------ one cooperative launch per step
+// The whole Gram-Schmidt part of one Lanczos step (alpha, y -= alpha v_j, every pass of dot, reduce and
+// update with the sqrt(2) test, normalisation) in a single cooperative launch: the grid synchronises
+// where the multi-kernel path ends one launch and starts the next, and each block walks row blocks
+// rb = blockIdx.x, blockIdx.x + gridDim.x, ... of the same partition (so partials, summation orders
+// and results do not depend on the grid size).  Every block computes the norms of the test from the
+// same partials in the same order, so all blocks take the same decision.  nrm2 holds two slots of
+// nblk norm partials, alternating between passes.
+template <typename R>
+__device__ R update_rows(const GSArgs& a, int64_t p0, int64_t p1, const coef4* sc, cplx<R> (*red1)[32],
+                         cplx<R> (*red2)[32]) {
+  using C = cplx<R>;
+  const C* V = (const C*)a.V;
+  C* y = (C*)a.y;
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int64_t n = a.n, h = a.h;
+  const int j = a.j;
+  R nrm_r = 0;
+  for (int64_t pb = p0; pb < p1; pb += 32) {
+    const int64_t p = pb + lane;
+    const bool ok = p < p1;
+    C acc1 = mk<R>(0, 0), acc2 = mk<R>(0, 0);
+    if (ok) {
+      for (int i = q; i <= j; i += kColGroups) {
+        const C* vi = V + (int64_t)i * n;
+        const C v1 = vi[p], v2 = vi[h + p];
+        const C cv = mk<R>((R)sc[i].vr, (R)sc[i].vi);
+        const C cw = mk<R>((R)sc[i].wr, (R)sc[i].wi);
+        const C ncw = mk<R>(-cw.x, -cw.y);
+        acc1 = cfma(v1, cv, acc1);
+        acc1 = cfmac(v2, ncw, acc1);
+        acc2 = cfma(v2, cv, acc2);
+        acc2 = cfmac(v1, cw, acc2);
+      }
+    }
+    red1[q][lane] = acc1;
+    red2[q][lane] = acc2;
+    __syncthreads();
+    if (q == 0 && ok) {
+      C s1 = red1[0][lane], s2 = red2[0][lane];
+#pragma unroll
+      for (int g = 1; g < kColGroups; ++g) { s1 = cadd(s1, red1[g][lane]); s2 = cadd(s2, red2[g][lane]); }
+      const C y1 = csub(y[p], s1), y2 = csub(y[h + p], s2);
+      y[p] = y1;
+      y[h + p] = y2;
+      nrm_r += cabs2w(y1) + cabs2w(y2);
+    }
+    __syncthreads();
+  }
+  return nrm_r;
+}
+
+// sqrt of the sum of nblk partials, the same fixed order in every block
+__device__ __forceinline__ double coop_norm(const double* part, int nblk, double* sh) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += kGsThreads) s += part[b];
+  return sqrt(block_sum(s, sh));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kGsThreads, 3)
+gs_step_coop_kernel(GSArgs a, const double2* __restrict__ alpha_part, int n_alpha_part, int passes,
+                    double* __restrict__ nrm2) {
+  using C = cplx<R>;
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[32];
+  __shared__ C red1[kColGroups][32], red2[kColGroups][32];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  R* dred = (R*)dyn_smem;
+  coef4* sc = (coef4*)(dyn_smem + dot_smem<R>());
+  const int j = a.j;
+  const int64_t h = a.h;
+  const int nblk = a.nblk;
+  StepState* st = a.st;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  // alpha = Re(v_j^H A v_j) from the product's partials (every block, same order)
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < n_alpha_part; i += kGsThreads) {
+    ar += alpha_part[i].x;
+    ai += alpha_part[i].y;
+  }
+  ar = block_sum(ar, sh);
+  ai = block_sum(ai, sh);
+  double tmax = st->tmax;
+  tmax = fmax(tmax, fabs(ar));
+  if (j > 0) tmax = fmax(tmax, fabs(a.T[(int64_t)j * a.ldt + j - 1]));
+  if (lead) {
+    a.T[(int64_t)j * a.ldt + j] = ar;
+    st->alpha_im = ai;
+    st->done = 0;
+    st->tmax = tmax;
+    st->n_passes += 1;
+    st->units_first += (double)(j + 1) * (double)h;
+  }
+  const R alpha = (R)ar;
+  const C* vj = (const C*)a.V + (int64_t)j * a.n;
+  C* y = (C*)a.y;
+  for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {   // y -= alpha v_j; b0 partials; pass-1 dots
+    const int64_t p0 = (int64_t)rb * a.rows_per_block;
+    const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+    R nrm_r = 0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kGsThreads) {
+      C y1 = y[p], y2 = y[h + p];
+      const C v1 = vj[p], v2 = vj[h + p];
+      y1.x -= alpha * v1.x; y1.y -= alpha * v1.y;
+      y2.x -= alpha * v2.x; y2.y -= alpha * v2.y;
+      y[p] = y1;
+      y[h + p] = y2;
+      nrm_r += cabs2w(y1) + cabs2w(y2);
+    }
+    const double nb = block_sum((double)nrm_r, sh);
+    if (threadIdx.x == 0) nrm2[rb] = nb;
+    dot_body<R, R>(a, p0, p1, dred, rb);
+  }
+  double bref = 0.0, beta = 0.0;
+  for (int pass = 1;; ++pass) {
+    grid.sync();                                           // dot partials and norm partials complete
+    if (pass == 1) {
+      bref = coop_norm(nrm2, nblk, sh);                    // b0
+      if (lead) st->nrm[0] = bref;
+    }
+    for (int c = blockIdx.x; c <= j; c += gridDim.x) {     // coefficients of column c
+      const coef4* src = (const coef4*)a.part_dot + (int64_t)c * nblk;
+      double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      for (int b = threadIdx.x; b < nblk; b += kGsThreads) {
+        const coef4 cc = src[b];
+        s0 += cc.vr; s1 += cc.vi; s2 += cc.wr; s3 += cc.wi;
+      }
+      s0 = block_sum(s0, sh); s1 = block_sum(s1, sh); s2 = block_sum(s2, sh); s3 = block_sum(s3, sh);
+      if (threadIdx.x == 0) {
+        coef4 cc; cc.vr = s0; cc.vi = s1; cc.wr = a.no_w ? 0.0 : s2; cc.wi = a.no_w ? 0.0 : s3;
+        a.coef[c] = cc;
+      }
+    }
+    grid.sync();                                           // coefficients complete
+    for (int i = threadIdx.x; i <= j; i += kGsThreads) sc[i] = a.coef[i];
+    __syncthreads();
+    double* slot = nrm2 + (size_t)(pass & 1) * nblk;
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
+      const int64_t p0 = (int64_t)rb * a.rows_per_block;
+      const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+      const double nb = block_sum((double)update_rows<R>(a, p0, p1, sc, red1, red2), sh);
+      if (threadIdx.x == 0) slot[rb] = nb;
+    }
+    if (lead) st->units_update += (double)(j + 1) * (double)h;
+    grid.sync();                                           // updated y and its norm partials complete
+    const double b1 = coop_norm(slot, nblk, sh);
+    if (lead && pass < 8) st->nrm[pass] = b1;
+    if (kSqrt2 * b1 > bref || pass >= passes) {            // the sqrt(2) test, or the pass cap
+      beta = b1;
+      break;
+    }
+    bref = b1;
+    if (lead) {
+      st->n_passes += 1;
+      st->units_dot += (double)(j + 1) * (double)h;
+    }
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {  // dots of the next pass on this block's rows
+      const int64_t p0 = (int64_t)rb * a.rows_per_block;
+      const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+      dot_body<R, R>(a, p0, p1, dred, rb);
+    }
+  }
+  // normalise: v_{j+1} = y / beta, t_{j+1,j} = beta; breakdown below 1e-14 max(max|t|, 1)
+  const bool brk = !(beta > 1e-14 * fmax(tmax, 1.0));
+  const R inv = brk ? (R)0 : (R)(1.0 / beta);
+  C* v = (C*)a.V + (int64_t)(j + 1) * a.n;
+  for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
+    const int64_t p0 = (int64_t)rb * a.rows_per_block;
+    const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kGsThreads) {
+      v[p] = cscale(y[p], inv);
+      v[h + p] = cscale(y[h + p], inv);
+    }
+  }
+  if (lead) {
+    a.T[(int64_t)(j + 1) * a.ldt + j] = beta;
+    if (j + 1 < a.m) a.T[(int64_t)j * a.ldt + j + 1] = beta;
+    st->beta = beta;
+    st->done = 1;
+    if (brk) st->status = 5;
+  }
+}
+
 int gs_blocks(int64_t h, int* rows_per_block) {
   // Row tiles of 32 row pairs, about four blocks per SM.
   const int64_t tiles = (h + 31) / 32;
@@ -382,8 +573,6 @@ int gs_blocks(int64_t h, int* rows_per_block) {
   return (int)((h + rpb - 1) / rpb);
 }
 
-template <typename P>
-constexpr size_t dot_smem() { return (size_t)kColGroups * 4 * dot_cols<P>() * 33 * sizeof(P); }
 
 template <typename R>
 cudaError_t launch_gs_first(const GSArgs& a, const double2* alpha_part, int n_alpha_part, cudaStream_t s) {
@@ -462,6 +651,41 @@ cudaError_t launch_links_soa(const void* in, void* out, int64_t vol, cudaStream_
   return cudaGetLastError();
 }
 
+template <typename R>
+size_t gs_coop_smem(int m) { return dot_smem<R>() + (size_t)(m + 1) * sizeof(coef4); }
+
+template <typename R>
+cudaError_t gs_coop_grid(int m, int nblk, int* grid) {
+  int dev = 0, nsm = 0, coop = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const size_t sm = gs_coop_smem<R>(m);
+  if ((e = cudaFuncSetAttribute(gs_step_coop_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gs_step_coop_kernel<R>, kGsThreads, sm)) != cudaSuccess)
+    return e;
+  *grid = (coop && per > 0) ? (nblk < per * nsm ? nblk : per * nsm) : 0;
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t launch_gs_step_coop(const GSArgs& a, const double2* alpha_part, int n_alpha_part, int passes,
+                                double* nrm2, int grid, cudaStream_t s) {
+  GSArgs aa = a;
+  const double2* ap = alpha_part;
+  int na = n_alpha_part, ps = passes;
+  double* nr = nrm2;
+  void* args[] = {&aa, &ap, &na, &ps, &nr};
+  return cudaLaunchCooperativeKernel((const void*)gs_step_coop_kernel<R>, dim3(grid), dim3(kGsThreads), args,
+                                     gs_coop_smem<R>(a.m), s);
+}
+template cudaError_t gs_coop_grid<double>(int, int, int*);
+template cudaError_t gs_coop_grid<float>(int, int, int*);
+template cudaError_t launch_gs_step_coop<double>(const GSArgs&, const double2*, int, int, double*, int, cudaStream_t);
+template cudaError_t launch_gs_step_coop<float>(const GSArgs&, const double2*, int, int, double*, int, cudaStream_t);
 template cudaError_t launch_gs_first<double>(const GSArgs&, const double2*, int, cudaStream_t);
 template cudaError_t launch_gs_first<float>(const GSArgs&, const double2*, int, cudaStream_t);
 template cudaError_t launch_gs_update<float>(const GSArgs&, cudaStream_t);

@@ -98,7 +98,7 @@ cudaError_t launch_links_df(const void* in, void* out, int64_t vol, cudaStream_t
 // Kernel classes for the optional per-kernel profile.
 enum KernelTag {
   K_MATVEC = 0, K_GS_FIRST, K_GS_REDUCE, K_GS_UPDATE, K_GS_DOT, K_GS_NORMALIZE, K_RITZ, K_ROTATE,
-  K_RESID, K_SHRINK, K_OTHER, K_RITZ_FALLBACK, K_FILTER, K_NTAGS
+  K_RESID, K_SHRINK, K_OTHER, K_RITZ_FALLBACK, K_FILTER, K_GS_STEP, K_NTAGS
 };
 template <typename R>
 cudaError_t launch_fill_ones(void* v, int64_t n, cudaStream_t s);
@@ -207,6 +207,15 @@ cudaError_t launch_resid_part(const void* y, const void* x, const double* lam, i
                               cudaStream_t s);
 // out[i][k] (k <= degree) = Jackson-damped Chebyshev coefficients of the step [x <= tau[i]] (FP32).
 cudaError_t launch_damped_step(const double* tau, int count, int degree, float* out, cudaStream_t s);
+
+// The whole Gram-Schmidt part of one Lanczos step (alpha, every pass, normalisation) as one
+// cooperative launch (gs.cu).  gs_coop_grid: the grid for a phase of basis size m and nblk row blocks
+// (0 if the device cannot launch it cooperatively).  nrm2: 2 * nblk doubles of scratch.
+template <typename R>
+cudaError_t gs_coop_grid(int m, int nblk, int* grid);
+template <typename R>
+cudaError_t launch_gs_step_coop(const GSArgs& a, const double2* alpha_part, int n_alpha_part, int passes,
+                                double* nrm2, int grid, cudaStream_t s);
 
 // Sets the thread-local text returned by jtrlan_last_error().
 void set_last_error(const char* msg);
