@@ -151,7 +151,8 @@ struct jtrlan_ctx {
   int* h_order = nullptr;
   double* h_misc = nullptr;
   int gs_nblk = 0, gs_rpb = 0;
-  int coop64 = 0, coop32 = 0;      // grids of the cooperative Gram-Schmidt step (0: multi-kernel path)
+  int coop64 = 0, coop32 = 0, coopdf = 0;   // row blocks (= CTAs) of the cooperative Gram-Schmidt step; 0: not used
+  int coop_rpb = 0, coop_rpb_df = 0;        // its rows per block
   double fc = 0.0, fe = 1.0;       // filter window centre and half-width
   Profiler prof;
   double work_base[3] = {};        // device work counters carried across solve phases
@@ -375,15 +376,54 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
     JT_TRY(c->dalloc(&ph.alpha_part, (size_t)nb * sizeof(double2)));
     JT_TRY(c->dalloc(&ph.resid_part, (size_t)std::max(nb, ph.mv_nblk * c->nev) * sizeof(double)));
   }
-  if (!c->mixed) JT_CUDA(gs_coop_grid<double>(m, c->gs_nblk, &c->coop64));
-  if (prm->precision == JTRLAN_MIXED) JT_CUDA(gs_coop_grid<float>(m, c->gs_nblk, &c->coop32));
+  {  // cooperative Gram-Schmidt step: its own row partition, one row block per resident CTA
+    int dev = 0, nsm = 0;
+    JT_CUDA(cudaGetDevice(&dev));
+    JT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t tiles = (c->h + 31) / 32;
+    auto part = [&](int per, int* rpb, int* nb) {   // rows per block and row blocks for per CTAs per SM
+      const int64_t G = (int64_t)per * nsm;
+      const int64_t tpb = (tiles + G - 1) / G;
+      *rpb = (int)(32 * (tpb < 1 ? 1 : tpb));
+      *nb = (int)((c->h + *rpb - 1) / *rpb);
+    };
+    int per = 0;
+    if (!c->mixed) {
+      JT_CUDA(gs_coop_occupancy<double>(m, &per));
+      if (per > 0) part(per, &c->coop_rpb, &c->coop64);
+    }
+    if (prm->precision == JTRLAN_MIXED) {
+      JT_CUDA(gs_coop_occupancy<float>(m, &per));
+      if (per > 0) part(per, &c->coop_rpb, &c->coop32);
+    }
+    if (c->mixed) {   // the shared memory grows with rows_per_block: size it, then check it still fits
+      GSArgs g{};
+      g.m = m;
+      g.rows_per_block = (int)(32 * ((tiles + 2 * nsm - 1) / (2 * nsm)));
+      // too many rows for one CTA's shared memory (large lattices): keep the multi-kernel path
+      if (gsdf_coop_occupancy(g, &per) != cudaSuccess) {
+        cudaGetLastError();
+        per = 0;
+      }
+      if (per > 0) {
+        part(per, &c->coop_rpb_df, &c->coopdf);
+        g.rows_per_block = c->coop_rpb_df;
+        if (gsdf_coop_occupancy(g, &per) != cudaSuccess) {
+          cudaGetLastError();
+          per = 0;
+        }
+        if ((int64_t)per * nsm < c->coopdf) c->coopdf = 0;
+      }
+    }
+  }
+  const int nblk_max = std::max(c->gs_nblk, std::max(std::max(c->coop64, c->coop32), c->coopdf));
   JT_TRY(c->dalloc(&c->T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
   JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));
   JT_TRY(c->dalloc(&c->Z, (size_t)m * m * sizeof(double)));
   JT_TRY(c->dalloc(&c->ritz_ws, (size_t)2 * mp * mp * sizeof(double)));
   JT_TRY(c->dalloc(&c->ritz_flags, (size_t)(m + 1) * sizeof(int)));
-  JT_TRY(c->dalloc(&c->part_dot, (size_t)(m + 1) * c->gs_nblk * sizeof(coef4)));
-  JT_TRY(c->dalloc(&c->part_nrm, (size_t)2 * c->gs_nblk * sizeof(double)));   // two slots (cooperative step)
+  JT_TRY(c->dalloc(&c->part_dot, (size_t)(m + 1) * nblk_max * sizeof(coef4)));
+  JT_TRY(c->dalloc(&c->part_nrm, (size_t)2 * nblk_max * sizeof(double)));   // two slots (cooperative step)
   JT_TRY(c->dalloc(&c->coef, (size_t)(m + 1) * sizeof(coef4)));
   JT_TRY(c->dalloc(&c->st, sizeof(StepState)));
   JT_TRY(c->dalloc(&c->d_res, (size_t)c->nev * sizeof(double)));
@@ -554,6 +594,14 @@ jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1,
     a.j = j;
     if (ph.df) {
       // compensated FP32 reorthogonalisation of an FP64 vector against a (hi, lo) basis; see gsdf.cu
+      if (c->coopdf > 0) {   // the whole step in one cooperative launch, on its own row partition
+        GSArgs ac = a;
+        ac.nblk = c->coopdf;
+        ac.rows_per_block = c->coop_rpb_df;
+        LAUNCH(K_GS_STEP, launch_gsdf_step_coop(ac, ph.x, (const double2*)ph.alpha_part, mv_parts, c->gs_passes,
+                                                 c->part_nrm, c->coopdf, s));
+        continue;
+      }
       LAUNCH(K_GS_FIRST, launch_gsdf_first(a, ph.x, (const double2*)ph.alpha_part, mv_parts, s));
       LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
       LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
@@ -565,8 +613,11 @@ jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1,
       LAUNCH(K_GS_NORMALIZE, launch_gsdf_normalize(a, ph.x, s));
     } else {
       const int coop = std::is_same<R, float>::value ? c->coop32 : c->coop64;
-      if (coop > 0) {   // the whole step in one cooperative launch
-        LAUNCH(K_GS_STEP, launch_gs_step_coop<R>(a, (const double2*)ph.alpha_part, mv_parts, c->gs_passes,
+      if (coop > 0) {   // the whole step in one cooperative launch, on its own row partition
+        GSArgs ac = a;
+        ac.nblk = coop;
+        ac.rows_per_block = c->coop_rpb;
+        LAUNCH(K_GS_STEP, launch_gs_step_coop<R>(ac, (const double2*)ph.alpha_part, mv_parts, c->gs_passes,
                                                   c->part_nrm, coop, s));
         continue;
       }

@@ -655,19 +655,18 @@ template <typename R>
 size_t gs_coop_smem(int m) { return dot_smem<R>() + (size_t)(m + 1) * sizeof(coef4); }
 
 template <typename R>
-cudaError_t gs_coop_grid(int m, int nblk, int* grid) {
-  int dev = 0, nsm = 0, coop = 0, per = 0;
+cudaError_t gs_coop_occupancy(int m, int* per_sm) {
+  int dev = 0, coop = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const size_t sm = gs_coop_smem<R>(m);
   if ((e = cudaFuncSetAttribute(gs_step_coop_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
       cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gs_step_coop_kernel<R>, kGsThreads, sm)) != cudaSuccess)
     return e;
-  *grid = (coop && per > 0) ? (nblk < per * nsm ? nblk : per * nsm) : 0;
+  *per_sm = coop ? per : 0;
   return cudaSuccess;
 }
 
@@ -682,8 +681,8 @@ cudaError_t launch_gs_step_coop(const GSArgs& a, const double2* alpha_part, int 
   return cudaLaunchCooperativeKernel((const void*)gs_step_coop_kernel<R>, dim3(grid), dim3(kGsThreads), args,
                                      gs_coop_smem<R>(a.m), s);
 }
-template cudaError_t gs_coop_grid<double>(int, int, int*);
-template cudaError_t gs_coop_grid<float>(int, int, int*);
+template cudaError_t gs_coop_occupancy<double>(int, int*);
+template cudaError_t gs_coop_occupancy<float>(int, int*);
 template cudaError_t launch_gs_step_coop<double>(const GSArgs&, const double2*, int, int, double*, int, cudaStream_t);
 template cudaError_t launch_gs_step_coop<float>(const GSArgs&, const double2*, int, int, double*, int, cudaStream_t);
 template cudaError_t launch_gs_first<double>(const GSArgs&, const double2*, int, cudaStream_t);

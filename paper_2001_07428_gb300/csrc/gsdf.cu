@@ -12,6 +12,8 @@
 //
 // Layout: V4[col * n + i] = {hi.re, hi.im, lo.re, lo.im} (float4); xbuf holds v_j in FP64 for the
 // FP64 matvec.  The kernel sequence and the device-side exit test mirror gs.cu.
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace jtr {
@@ -60,7 +62,7 @@ __device__ __forceinline__ double2 join(float4 f) {
 // rows [p0, p1); y has been split into ys (shared, [2][rows]).  Warp q takes chunks of 8 columns;
 // each lane keeps 8 x 4 (sum, error) pairs, combines them to FP64 and the warp transposes them
 // through shared memory so that lane k adds up accumulator k.
-__device__ void dfdot_body(const GSArgs& a, int64_t p0, int64_t p1, const float4* ys, float* red) {
+__device__ void dfdot_body(const GSArgs& a, int64_t p0, int64_t p1, const float4* ys, float* red, int rb) {
   const float4* V = (const float4*)a.V;
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   const int64_t n = a.n, h = a.h, rows = p1 - p0;
@@ -126,7 +128,7 @@ __device__ void dfdot_body(const GSArgs& a, int64_t p0, int64_t p1, const float4
     __syncwarp();
     const int c = lane >> 2, t = lane & 3;
     if (lane < 4 * kCols && c < ncol)
-      a.part_dot[((int64_t)(c0 + c) * a.nblk + blockIdx.x) * 4 + t] = (double)S + (double)E;
+      a.part_dot[((int64_t)(c0 + c) * a.nblk + rb) * 4 + t] = (double)S + (double)E;
   }
 }
 
@@ -183,7 +185,7 @@ gsdf_first_kernel(GSArgs a, const double2* __restrict__ x, const double2* __rest
   float4* ys = (float4*)dyn;
   float* red = (float*)(ys + 2 * a.rows_per_block);
   split_rows(a, p0, p1, ys);
-  dfdot_body(a, p0, p1, ys, red);
+  dfdot_body(a, p0, p1, ys, red, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kThreads, kDotMinBlocks) gsdf_dot_kernel(GSArgs a, int pass) {
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, kDotMinBlocks) gsdf_dot_kernel(GSArg
   float4* ys = (float4*)dyn;
   float* red = (float*)(ys + 2 * a.rows_per_block);
   split_rows(a, p0, p1, ys);
-  dfdot_body(a, p0, p1, ys, red);
+  dfdot_body(a, p0, p1, ys, red, blockIdx.x);
 }
 
 // y -= V c_v + W c_w: the correction is accumulated per row in compensated FP32 over this warp's
@@ -330,6 +332,208 @@ __global__ void __launch_bounds__(kThreads) gsdf_normalize_kernel(GSArgs a, doub
     const int j = a.j;
     a.T[(int64_t)(j + 1) * a.ldt + j] = beta;
     if (j + 1 < a.m) a.T[(int64_t)j * a.ldt + j + 1] = beta;
+    if (brk) st->status = 5;
+  }
+}
+
+// ------------------------------------------------------------------ one cooperative launch per step
+// The compensated-FP32 Gram-Schmidt of one Lanczos step (alpha, every pass with the sqrt(2) test,
+// normalisation) as one cooperative launch, like gs_step_coop_kernel in gs.cu: grid-wide barriers
+// where the multi-kernel path ends one launch and starts the next; each block walks row blocks
+// rb = blockIdx.x, blockIdx.x + gridDim.x, ... of the same partition; every block takes the test from
+// the same partials in the same order; nrm2 holds two slots of nblk norm partials.
+__device__ double dfupdate_rows(const GSArgs& a, int64_t p0, int64_t p1, const float4* scf, float (*red_s)[32][4],
+                                float (*red_e)[32][4]) {
+  const float4* V = (const float4*)a.V;
+  double2* y = (double2*)a.y;
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int64_t n = a.n, h = a.h;
+  const int j = a.j;
+  double nrm = 0.0;
+  for (int64_t pb = p0; pb < p1; pb += 32) {
+    const int64_t p = pb + lane;
+    const bool ok = p < p1;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+    if (ok) {
+      for (int i = q; i <= j; i += kGroups) {
+        const float4 v1 = V[(int64_t)i * n + p], v2 = V[(int64_t)i * n + h + p];
+        const float4 cv = scf[2 * i], cw = scf[2 * i + 1];
+        df_acc(s[0], e[0], v1.x, v1.z, cv.x, cv.z);  df_sub(s[0], e[0], v1.y, v1.w, cv.y, cv.w);
+        df_sub(s[0], e[0], v2.x, v2.z, cw.x, cw.z);  df_sub(s[0], e[0], v2.y, v2.w, cw.y, cw.w);
+        df_acc(s[1], e[1], v1.x, v1.z, cv.y, cv.w);  df_acc(s[1], e[1], v1.y, v1.w, cv.x, cv.z);
+        df_sub(s[1], e[1], v2.x, v2.z, cw.y, cw.w);  df_acc(s[1], e[1], v2.y, v2.w, cw.x, cw.z);
+        df_acc(s[2], e[2], v2.x, v2.z, cv.x, cv.z);  df_sub(s[2], e[2], v2.y, v2.w, cv.y, cv.w);
+        df_acc(s[2], e[2], v1.x, v1.z, cw.x, cw.z);  df_acc(s[2], e[2], v1.y, v1.w, cw.y, cw.w);
+        df_acc(s[3], e[3], v2.x, v2.z, cv.y, cv.w);  df_acc(s[3], e[3], v2.y, v2.w, cv.x, cv.z);
+        df_acc(s[3], e[3], v1.x, v1.z, cw.y, cw.w);  df_sub(s[3], e[3], v1.y, v1.w, cw.x, cw.z);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      red_s[q][lane][t] = s[t];
+      red_e[q][lane][t] = e[t];
+    }
+    __syncthreads();
+    if (q == 0 && ok) {
+      double c[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float S = red_s[0][lane][t], E = red_e[0][lane][t];
+#pragma unroll
+        for (int g = 1; g < kGroups; ++g) {
+          float u, ue;
+          two_sum(S, red_s[g][lane][t], u, ue);
+          S = u;
+          E = __fadd_rn(E, __fadd_rn(ue, red_e[g][lane][t]));
+        }
+        c[t] = (double)S + (double)E;
+      }
+      double2 y1 = y[p], y2 = y[h + p];
+      y1.x -= c[0]; y1.y -= c[1];
+      y2.x -= c[2]; y2.y -= c[3];
+      y[p] = y1;
+      y[h + p] = y2;
+      nrm += cabs2(y1) + cabs2(y2);
+    }
+    __syncthreads();
+  }
+  return nrm;
+}
+
+__device__ __forceinline__ double coop_norm_df(const double* part, int nblk, double* sh) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += kThreads) s += part[b];
+  return sqrt(block_sum(s, sh));
+}
+
+__global__ void __launch_bounds__(kThreads, 3)
+gsdf_step_coop_kernel(GSArgs a, double2* __restrict__ x, const double2* __restrict__ alpha_part, int n_alpha_part,
+                      int passes, double* __restrict__ nrm2) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ double sh[32];
+  __shared__ float red_s[kGroups][32][4], red_e[kGroups][32][4];
+  float4* ys = (float4*)dyn;
+  float* red = (float*)(ys + 2 * a.rows_per_block);
+  float4* scf = (float4*)(red + kGroups * 2 * (4 * kCols) * 33);
+  const int j = a.j;
+  const int64_t h = a.h;
+  const int nblk = a.nblk;
+  StepState* st = a.st;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < n_alpha_part; i += kThreads) {
+    ar += alpha_part[i].x;
+    ai += alpha_part[i].y;
+  }
+  ar = block_sum(ar, sh);
+  ai = block_sum(ai, sh);
+  double tmax = fmax(st->tmax, fabs(ar));
+  if (j > 0) tmax = fmax(tmax, fabs(a.T[(int64_t)j * a.ldt + j - 1]));
+  if (lead) {
+    a.T[(int64_t)j * a.ldt + j] = ar;
+    st->alpha_im = ai;
+    st->done = 0;
+    st->tmax = tmax;
+    st->n_passes += 1;
+    st->units_first += (double)(j + 1) * (double)h;
+  }
+  double2* y = (double2*)a.y;
+  for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {   // y -= alpha v_j in FP64; b0; pass-1 dots
+    const int64_t p0 = (int64_t)rb * a.rows_per_block;
+    const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+    double nrm = 0.0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
+      double2 y1 = y[p], y2 = y[h + p];
+      const double2 v1 = x[p], v2 = x[h + p];
+      y1.x -= ar * v1.x; y1.y -= ar * v1.y;
+      y2.x -= ar * v2.x; y2.y -= ar * v2.y;
+      y[p] = y1;
+      y[h + p] = y2;
+      nrm += cabs2(y1) + cabs2(y2);
+    }
+    nrm = block_sum(nrm, sh);
+    if (threadIdx.x == 0) nrm2[rb] = nrm;
+    split_rows(a, p0, p1, ys);
+    dfdot_body(a, p0, p1, ys, red, rb);
+    __syncthreads();                                       // ys and red are reused by the next row block
+  }
+  double bref = 0.0, beta = 0.0;
+  for (int pass = 1;; ++pass) {
+    grid.sync();
+    if (pass == 1) {
+      bref = coop_norm_df(nrm2, nblk, sh);
+      if (lead) st->nrm[0] = bref;
+    }
+    for (int c = blockIdx.x; c <= j; c += gridDim.x) {
+      const coef4* src = (const coef4*)a.part_dot + (int64_t)c * nblk;
+      double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      for (int b = threadIdx.x; b < nblk; b += kThreads) {
+        const coef4 cc = src[b];
+        s0 += cc.vr; s1 += cc.vi; s2 += cc.wr; s3 += cc.wi;
+      }
+      s0 = block_sum(s0, sh); s1 = block_sum(s1, sh); s2 = block_sum(s2, sh); s3 = block_sum(s3, sh);
+      if (threadIdx.x == 0) {
+        coef4 cc; cc.vr = s0; cc.vi = s1; cc.wr = a.no_w ? 0.0 : s2; cc.wi = a.no_w ? 0.0 : s3;
+        a.coef[c] = cc;
+      }
+    }
+    grid.sync();
+    for (int i = threadIdx.x; i <= j; i += kThreads) {
+      const coef4 cc = a.coef[i];
+      scf[2 * i] = split(make_double2(cc.vr, cc.vi));
+      scf[2 * i + 1] = split(make_double2(cc.wr, cc.wi));
+    }
+    __syncthreads();
+    double* slot = nrm2 + (size_t)(pass & 1) * nblk;
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
+      const int64_t p0 = (int64_t)rb * a.rows_per_block;
+      const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+      const double nb = block_sum(dfupdate_rows(a, p0, p1, scf, red_s, red_e), sh);
+      if (threadIdx.x == 0) slot[rb] = nb;
+    }
+    if (lead) st->units_update += (double)(j + 1) * (double)h;
+    grid.sync();
+    const double b1 = coop_norm_df(slot, nblk, sh);
+    if (lead && pass < 8) st->nrm[pass] = b1;
+    if (kSqrt2 * b1 > bref || pass >= passes) {
+      beta = b1;
+      break;
+    }
+    bref = b1;
+    if (lead) {
+      st->n_passes += 1;
+      st->units_dot += (double)(j + 1) * (double)h;
+    }
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
+      const int64_t p0 = (int64_t)rb * a.rows_per_block;
+      const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+      split_rows(a, p0, p1, ys);
+      dfdot_body(a, p0, p1, ys, red, rb);
+      __syncthreads();
+    }
+  }
+  const bool brk = !(beta > 1e-14 * fmax(tmax, 1.0));
+  const double inv = brk ? 0.0 : 1.0 / beta;
+  float4* v = (float4*)a.V + (int64_t)(j + 1) * a.n;
+  for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
+    const int64_t p0 = (int64_t)rb * a.rows_per_block;
+    const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
+      const double2 y1 = y[p], y2 = y[h + p];
+      const double2 v1 = make_double2(y1.x * inv, y1.y * inv), v2 = make_double2(y2.x * inv, y2.y * inv);
+      v[p] = split(v1);
+      v[h + p] = split(v2);
+      x[p] = v1;
+      x[h + p] = v2;
+    }
+  }
+  if (lead) {
+    a.T[(int64_t)(j + 1) * a.ldt + j] = beta;
+    if (j + 1 < a.m) a.T[(int64_t)j * a.ldt + j + 1] = beta;
+    st->beta = beta;
+    st->done = 1;
     if (brk) st->status = 5;
   }
 }
@@ -677,6 +881,35 @@ cudaError_t launch_gsdf_first(const GSArgs& a, const void* x, const double2* alp
   if (e != cudaSuccess) return e;
   gsdf_first_kernel<<<a.nblk, kThreads, sm, s>>>(a, (const double2*)x, alpha_part, n_alpha_part);
   return cudaGetLastError();
+}
+
+size_t gsdf_coop_smem(const GSArgs& a) { return dot_smem(a) + (size_t)2 * (a.m + 1) * sizeof(float4); }
+
+cudaError_t gsdf_coop_occupancy(const GSArgs& a, int* per_sm) {
+  int dev = 0, coop = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+  const size_t sm = gsdf_coop_smem(a);
+  if ((e = cudaFuncSetAttribute(gsdf_step_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gsdf_step_coop_kernel, kThreads, sm)) != cudaSuccess)
+    return e;
+  *per_sm = coop ? per : 0;
+  return cudaSuccess;
+}
+
+cudaError_t launch_gsdf_step_coop(const GSArgs& a, void* x, const double2* alpha_part, int n_alpha_part, int passes,
+                                  double* nrm2, int grid, cudaStream_t s) {
+  GSArgs aa = a;
+  double2* xx = (double2*)x;
+  const double2* ap = alpha_part;
+  int na = n_alpha_part, ps = passes;
+  double* nr = nrm2;
+  void* args[] = {&aa, &xx, &ap, &na, &ps, &nr};
+  return cudaLaunchCooperativeKernel((const void*)gsdf_step_coop_kernel, dim3(grid), dim3(kThreads), args,
+                                     gsdf_coop_smem(a), s);
 }
 
 cudaError_t launch_gsdf_dot(const GSArgs& a, int pass, cudaStream_t s) {

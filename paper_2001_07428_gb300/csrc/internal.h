@@ -209,13 +209,20 @@ cudaError_t launch_resid_part(const void* y, const void* x, const double* lam, i
 cudaError_t launch_damped_step(const double* tau, int count, int degree, float* out, cudaStream_t s);
 
 // The whole Gram-Schmidt part of one Lanczos step (alpha, every pass, normalisation) as one
-// cooperative launch (gs.cu).  gs_coop_grid: the grid for a phase of basis size m and nblk row blocks
-// (0 if the device cannot launch it cooperatively).  nrm2: 2 * nblk doubles of scratch.
+// cooperative launch (gs.cu).  gs_coop_occupancy: resident blocks per SM for basis size m (0 if the
+// device cannot launch cooperatively).  The launch's grid is a.nblk: one row block per CTA, all
+// resident.  nrm2: 2 * a.nblk doubles of scratch.
 template <typename R>
-cudaError_t gs_coop_grid(int m, int nblk, int* grid);
+cudaError_t gs_coop_occupancy(int m, int* per_sm);
 template <typename R>
 cudaError_t launch_gs_step_coop(const GSArgs& a, const double2* alpha_part, int n_alpha_part, int passes,
                                 double* nrm2, int grid, cudaStream_t s);
+
+// The compensated-FP32 Gram-Schmidt of one Lanczos step as one cooperative launch (gsdf.cu); its
+// shared memory, so its occupancy, depends on rows_per_block and m of `a`.
+cudaError_t gsdf_coop_occupancy(const GSArgs& a, int* per_sm);
+cudaError_t launch_gsdf_step_coop(const GSArgs& a, void* x, const double2* alpha_part, int n_alpha_part, int passes,
+                                  double* nrm2, int grid, cudaStream_t s);
 
 // Sets the thread-local text returned by jtrlan_last_error().
 void set_last_error(const char* msg);
