@@ -49,6 +49,11 @@ BYTES_PER_UNIT = {"matvec": 84 * 16.0, "resid": 84 * 16.0, "gs_first": 32.0, "gs
                   "gs_update": 32.0, "gs_step": 32.0}
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the current
+# kernel (profiles/launches_stencil_8x8x8x8_fp64.md: gs_step_coop_kernel<double>, mean of 2 launches)
+NCU_TRAFFIC = {"gs_step": 13.66e6}
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -615,7 +620,7 @@ def run_gb300(args, rank, world, local_rank):
     if "tflops" in kernels[dom]:
         ach = kernels[dom]["tflops"]
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": round(FP64_PEAK_TFLOPS, 3),
-                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC.get(dom),
                 "peak_source": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     else:
         roof = {"kernel": dom, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
