@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -233,6 +234,70 @@ def stencil_apply_roofline(dims, reps=20, seed=4):
     gbs = algo / t / 1e9
     return {"lattice": list(dims), "us": round(t * 1e6, 2), "algorithmic_bytes": algo, "gbs": round(gbs, 1),
             "frac_of_hbm": round(gbs / hbm, 4), "hbm_peak_gbs": hbm, "peak_source": src}
+
+
+# ---------------------------------------------------------------- restart rotation on the tensor cores
+# (n, m, kk) of the lattices' mixed-precision solves: the rotation of the nev candidate Ritz vectors
+ROTATE_SHAPES = {"8x8x8x8": (24576, 60, 20), "16x16x16x16": (393216, 120, 50), "24x24x24x48": (3981312, 200, 100)}
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("bf16_tflops", 1900.0)), "measured (burst)"
+    return 1900.0, "fallback"
+
+
+def rotate_roofline(shape, reps=5, seed=6):
+    """Times jtrlan_rotate_df (V Z for a (hi, lo) basis V, n x m, and FP64 Z, m x kk) on the tensor
+    cores (path 0) and on the CUDA cores (path 1): median of `reps` calls, L2 flushed before each.  A
+    call also allocates and frees its scratch, computes the row exponents of V and splits Z (about
+    0.1 ms of the small case).  The tensor-core figure counts the BF16 MMA work issued: 28 digit
+    pairs x 2 x (2n rounded up to 128) x (m rounded up to 16) x (kk rounded up to 32)."""
+    import torch
+
+    from paper_2001_07428_gb300 import binding as B
+    n, m, kk = shape
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x = torch.randn(m, n, 2, dtype=torch.float64, device=dev, generator=g) / math.sqrt(2 * n)
+    hi = x.float()
+    lo = (x - hi.double()).float()
+    del x
+    V = torch.stack([hi[..., 0], hi[..., 1], lo[..., 0], lo[..., 1]], dim=-1).contiguous()
+    del hi, lo
+    Z = np.linalg.qr(np.random.default_rng(seed).standard_normal((m, m)))[0][:, :kk]
+    Zd = torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev)
+    out = [torch.empty(kk, n, dtype=torch.complex128, device=dev) for _ in range(2)]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for path in (0, 1):
+        B.jtrlan_rotate_df(V.data_ptr(), n, m, Zd.data_ptr(), kk, out[path].data_ptr(), path, stream.cuda_stream)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.jtrlan_rotate_df(V.data_ptr(), n, m, Zd.data_ptr(), kk, out[path].data_ptr(), path, stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        res[path] = statistics.median(ts)
+    diff = (out[0] - out[1]).abs().max().item()
+    del V, out
+    torch.cuda.empty_cache()
+    peak, src = bf16_peak()
+    mma = 28 * 2 * (-(-2 * n // 128) * 128) * (-(-m // 16) * 16) * (-(-kk // 32) * 32)
+    algo = 2 * (2 * n) * m * kk
+    tf = mma / res[0] / 1e12
+    return {"n": n, "m": m, "kk": kk, "tensor_ms": round(res[0] * 1e3, 3), "cuda_core_ms": round(res[1] * 1e3, 3),
+            "speedup": round(res[1] / res[0], 2), "max_abs_diff_between_paths": diff,
+            "roofline": {"bound": "tensor", "achieved": round(tf, 1), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(tf / peak, 4), "peak_source": src,
+                         "work": "BF16 MMA flops issued (28 digit pairs)"},
+            "fp64_equivalent_tflops": round(algo / res[0] / 1e12, 3)}
 
 
 # ---------------------------------------------------------------- learned polynomial filter
@@ -672,6 +737,7 @@ def run_gb300(args, rank, world, local_rank):
             "kernels": kernels,
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
     line["stencil_fp32"] = {k: stencil_apply_roofline(v) for k, v in STENCIL_LATTICES.items()}
+    line["rotate_tc"] = {k: rotate_roofline(v) for k, v in ROTATE_SHAPES.items()}
     if not args.no_learned:
         line["learned_filter"] = learned_compare(B, torch, "16x16x16x16", with_fp64=False)
     if not args.no_batched:
@@ -704,6 +770,8 @@ def main():
     ap.add_argument("--learned-only", default=None, choices=sorted(LEARNED_LATTICES),
                     help="only compare the learned-filter form with the unfiltered solver on this lattice")
     ap.add_argument("--with-fp64", action="store_true", help="with --learned-only: also time plain FP64")
+    ap.add_argument("--rotate-only", default=None, choices=sorted(ROTATE_SHAPES),
+                    help="only time the restart rotation of the (hi, lo) basis at this lattice's shape")
     ap.add_argument("--batched-only", action="store_true", help="only time the batched dense instances")
     ap.add_argument("--batch-count", type=int, default=None, help="with --batched-only: the first N instances")
     ap.add_argument("--batch-shape", default=None, help="with --batched-only: THREADS,CTAS_PER_SM instead of tuning")
@@ -725,6 +793,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.rotate_only:
+        print(json.dumps(rotate_roofline(ROTATE_SHAPES[args.rotate_only])), flush=True)
         return
     if args.stencil_only:
         print(json.dumps(stencil_apply_roofline(STENCIL_LATTICES[args.stencil_only])), flush=True)

@@ -38,7 +38,7 @@ typedef enum {
   JTRLAN_ENOTJSYM = 4,    /* the Lemma 1 self-check found the operator not J-symmetric */
   JTRLAN_EBREAKDOWN = 5,  /* Lanczos breakdown: beta below the breakdown threshold */
   JTRLAN_ENOCONV = 6,     /* max_restarts reached before nev pairs converged */
-  JTRLAN_ETIMEOUT = 7,    /* reserved: a bounded device-side wait ran out */
+  JTRLAN_ETIMEOUT = 7,    /* a bounded device-side wait ran out (tensor-core rotation) */
   JTRLAN_ESTATE = 8       /* call out of order (e.g. pairs before a successful solve) */
 } jtrlan_status;
 
@@ -133,6 +133,8 @@ typedef struct {
   const double* filter_final_coeffs;  /* host, filter_final_degree + 1 coefficients (copied) */
   int plain_trlan;    /* nonzero: the standard TRLAN the paper compares against (Algorithms 1 and 2
                          with W removed: Gram-Schmidt against V only) */
+  int rotate_simt;    /* nonzero: the restart rotation of a compensated-FP32 basis runs on the CUDA
+                         cores (jtrlan_rotate_df path 1) instead of the tensor cores */
 } jtrlan_params;
 
 /* Counters of the last solve (Sec. 3 counts only the Lanczos-step products as N_MV). */
@@ -252,6 +254,28 @@ jtrlan_status jtrlan_damped_step(const double* tau, int count, int degree, float
 jtrlan_status jtrlan_residual_norms_noalloc(const jtrlan_operator* op, const void* X, int64_t ldx,
                                             int ncols, const double* lambda, double* res,
                                             void* cuda_stream);
+
+/* Restart rotation of a compensated-FP32 basis: out = V Z.
+ *
+ * The thick-restart step of Algorithm 1 keeps the Ritz vectors V_m Z, Z the eigenvectors of T_m;
+ * this is that product for a basis held as (hi, lo) FP32 pairs, the layout of the
+ * JTRLAN_MIXED_REORTH and JTRLAN_MIXED solvers, with an FP64 result.
+ *   V: device, n x m complex numbers, column-major (column j at V + j n), each as float4
+ *     (re_hi, im_hi, re_lo, im_lo), the value being hi + lo; |V| < 2^127.
+ *   Z: device, m x kk FP64, column-major (column c at Z + c m); |Z| < 2^120.
+ *   out: device, n x kk complex128, column-major, written; must not overlap V or Z.
+ *   path: 0 = tensor cores (tcgen05, BF16 digit splitting with exact FP32 accumulation; needs
+ *     m <= 320), 1 = compensated FP32 on the CUDA cores (any m).
+ * Each entry agrees with the exact product of the given values to about 2^-49 m max_k |V_rk|
+ * max_k |Z_kc| on either path (on path 0 a row of the real view whose entries all lie below 2^-120
+ * is resolved to 2^-169 absolute instead; path 1 multiplies FP32 pairs, so there the bound needs
+ * every nonzero product |V_rk Z_kc| above 2^-100 and every |Z| below 2^100).  The call allocates and frees its scratch (row and column exponents,
+ * the BF16 digits of Z) and synchronises the stream.
+ * Errors: JTRLAN_EINVAL (null pointers, n < 1, m < 1, kk < 1, path 0 with m > 320, path not 0/1),
+ * JTRLAN_ENOMEM, JTRLAN_ECUDA, JTRLAN_ETIMEOUT (a bounded wait inside the tensor-core kernel ran
+ * out; the stream stays usable). */
+jtrlan_status jtrlan_rotate_df(const void* V, int64_t n, int m, const double* Z, int kk, void* out, int path,
+                               void* cuda_stream);
 
 /* ---- Batched dense solver: many independent dense operators of uneven order, one persistent launch.
  *

@@ -26,7 +26,7 @@ EXPORTED = ["jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jt
             "jtrlan_batch_results", "jtrlan_batch_vectors", "jtrlan_batch_destroy", "jtrlan_apply_filter", "jtrlan_bounds",
             "jtrlan_damped_step", "jtrlan_mlp_param_count", "jtrlan_mlp_create", "jtrlan_mlp_get_params",
             "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train",
-            "jtrlan_mlp_destroy"]
+            "jtrlan_mlp_destroy", "jtrlan_rotate_df"]
 NOALLOC_MAX_PARTIALS = 262144   # JTRLAN_NOALLOC_MAX_PARTIALS
 NOALLOC_MAX_COLS = 1024         # JTRLAN_NOALLOC_MAX_COLS
 
@@ -45,7 +45,8 @@ class jtrlan_params(ctypes.Structure):
                 ("v1", ctypes.c_void_p), ("check_jsym", ctypes.c_int), ("profile", ctypes.c_int),
                 ("filter_degree", ctypes.c_int), ("filter_coeffs", ctypes.c_void_p), ("filter_lo", ctypes.c_double),
                 ("filter_hi", ctypes.c_double), ("filter_final_degree", ctypes.c_int),
-                ("filter_final_coeffs", ctypes.c_void_p), ("plain_trlan", ctypes.c_int)]
+                ("filter_final_coeffs", ctypes.c_void_p), ("plain_trlan", ctypes.c_int),
+                ("rotate_simt", ctypes.c_int)]
 
 
 class jtrlan_stats(ctypes.Structure):
@@ -150,11 +151,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.c_float, ctypes.c_void_p]
     lib.jtrlan_mlp_destroy.argtypes = [ctypes.c_void_p]
     lib.jtrlan_mlp_destroy.restype = None
+    lib.jtrlan_rotate_df.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     for f in ("jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jtrlan_get_profile",
               "jtrlan_residual_norms_noalloc", "jtrlan_batch_create", "jtrlan_batch_set_shape",
               "jtrlan_batch_tune", "jtrlan_batch_solve", "jtrlan_batch_results", "jtrlan_batch_vectors",
               "jtrlan_apply_filter", "jtrlan_bounds", "jtrlan_damped_step", "jtrlan_mlp_create", "jtrlan_mlp_get_params",
-              "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train"):
+              "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train",
+              "jtrlan_rotate_df"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -266,6 +270,13 @@ def jtrlan_damped_step(tau_ptr: int, count: int, degree: int, out_ptr: int, stre
                                      ctypes.c_void_p(stream)))
 
 
+def jtrlan_rotate_df(V_ptr: int, n: int, m: int, Z_ptr: int, kk: int, out_ptr: int, path: int = 0, stream: int = 0):
+    """out (n x kk complex128) = V Z for a (hi, lo) basis V (n x m float4) and FP64 Z (m x kk); path 0 =
+    tensor cores, 1 = CUDA cores."""
+    _check(load().jtrlan_rotate_df(ctypes.c_void_p(V_ptr), int(n), int(m), ctypes.c_void_p(Z_ptr), int(kk),
+                                   ctypes.c_void_p(out_ptr), int(path), ctypes.c_void_p(stream)))
+
+
 def jtrlan_mlp_param_count(n_in: int, width: int, n_out: int) -> int:
     return int(load().jtrlan_mlp_param_count(int(n_in), int(width), int(n_out)))
 
@@ -328,7 +339,7 @@ def dense_operator(n, a11_ptr, a12_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
 
 def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_restarts=0,
            gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0, filter_coeffs=None, filter_window=None,
-           filter_final_coeffs=None, plain_trlan=0) -> jtrlan_params:
+           filter_final_coeffs=None, plain_trlan=0, rotate_simt=0) -> jtrlan_params:
     """filter_coeffs / filter_final_coeffs: float64 arrays g_0..g_d (kept alive on the struct until
     create copies them); filter_window: (lo, hi)."""
     p = jtrlan_params()
@@ -339,6 +350,7 @@ def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_
     p.check_jsym = int(check_jsym)
     p.profile = int(profile)
     p.plain_trlan = int(plain_trlan)
+    p.rotate_simt = int(rotate_simt)
     if filter_coeffs is not None:
         import numpy as np
         g = np.ascontiguousarray(filter_coeffs, dtype=np.float64)

@@ -153,6 +153,9 @@ struct jtrlan_ctx {
   int gs_nblk = 0, gs_rpb = 0;
   int coop64 = 0, coop32 = 0, coopdf = 0;   // row blocks (= CTAs) of the cooperative Gram-Schmidt step; 0: not used
   int coop_rpb = 0, coop_rpb_df = 0;        // its rows per block
+  TcWork tc{};                     // scratch of the tensor-core rotation (compensated-FP32 basis)
+  bool tc_on = false;
+  int* h_tcerr = nullptr;          // pinned copy of its error flag
   double fc = 0.0, fe = 1.0;       // filter window centre and half-width
   Profiler prof;
   double work_base[3] = {};        // device work counters carried across solve phases
@@ -326,6 +329,15 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
       const int nb = matvec_df_blocks(d);
       if (nb > c->pdf.mv_nblk) JT_TRY(c->dalloc(&c->pdf.alpha_part, (size_t)nb * sizeof(double2)));
     }
+  }
+  if (c->mixed && !prm->rotate_simt && m <= tc_rotate_max_m()) {   // restart rotation on the tensor cores
+    void* base = nullptr;
+    JT_TRY(c->dalloc(&base, tc_rotate_bytes(c->n, m, std::max(c->kk, 1))));
+    c->tc = tc_rotate_carve(base, c->n, m, std::max(c->kk, 1));
+    JT_CUDA(cudaMemsetAsync(c->tc.err, 0, sizeof(int), c->stream));
+    JT_TRY(c->halloc(&c->h_tcerr, sizeof(int)));
+    *c->h_tcerr = 0;
+    c->tc_on = true;
   }
   if (c->mixed) {  // the FP32 operator: links re-laid out structure-of-arrays, or FP32 dense blocks
     OpDev& q = c->p32.op;
@@ -682,7 +694,9 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
       if (ncols <= 0) return JTRLAN_OK;
       void* out = (char*)ph.Vtmp + (size_t)c0 * n * tcs;
       const double* Zc = c->Z + (size_t)c0 * m;
-      if (ph.df)
+      if (ph.df && c->tc_on)
+        LAUNCH(K_ROTATE, launch_rotate_tc(ph.V, n, m, Zc, ncols, out, c->tc, c0 == 0, s));
+      else if (ph.df)
         LAUNCH(K_ROTATE, launch_rotate_df(ph.V, n, m, Zc, ncols, out, s));
       else
         LAUNCH(K_ROTATE, launch_rotate<R>(ph.V, n, m, Zc, ncols, out, s));
@@ -692,8 +706,12 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     JT_TRY(rotate_cols(0, nev));
     LAUNCH(K_OTHER, launch_report(c->lam, c->Z, m, c->T, ldt, c->st, c->d_rep, s));
     JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * m + 8) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (ph.df && c->tc_on) JT_CUDA(cudaMemcpyAsync(c->h_tcerr, c->tc.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     JT_CUDA(cudaStreamSynchronize(s));
     JT_CUDA(c->prof.harvest());
+    if (ph.df && c->tc_on && *c->h_tcerr != 0)
+      return fail(JTRLAN_ETIMEOUT, "tensor-core rotation: a bounded wait ran out (code " +
+                                       std::to_string(*c->h_tcerr) + ")");
     stt.n_gs_passes += (int64_t)c->h_rep[2 * m + 2] - c->gs_pass_base;
     c->gs_pass_base = (int64_t)c->h_rep[2 * m + 2];
     c->work[K_GS_FIRST] = c->work_base[0] + c->h_rep[2 * m + 4];
@@ -1059,6 +1077,35 @@ jtrlan_status jtrlan_damped_step(const double* tau, int count, int degree, float
   if (count < 0 || degree < 0 || degree > 1024) return fail(JTRLAN_EINVAL, "need count >= 0 and 0 <= degree <= 1024");
   if (count > 0 && (!tau || !out)) return fail(JTRLAN_EINVAL, "null argument");
   JT_CUDA(launch_damped_step(tau, count, degree, out, (cudaStream_t)cuda_stream));
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_rotate_df(const void* V, int64_t n, int m, const double* Z, int kk, void* out, int path,
+                               void* cuda_stream) {
+  if (!V || !Z || !out) return fail(JTRLAN_EINVAL, "null argument");
+  if (n < 1 || m < 1 || kk < 1) return fail(JTRLAN_EINVAL, "need n, m, kk >= 1");
+  if (path != 0 && path != 1) return fail(JTRLAN_EINVAL, "path must be 0 (tensor cores) or 1 (CUDA cores)");
+  if (path == 0 && m > tc_rotate_max_m())
+    return fail(JTRLAN_EINVAL, "tensor-core rotation needs m <= " + std::to_string(tc_rotate_max_m()));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (path == 1) {
+    JT_CUDA(launch_rotate_df(V, n, m, Z, kk, out, s));
+    JT_CUDA(cudaStreamSynchronize(s));
+    return JTRLAN_OK;
+  }
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, tc_rotate_bytes(n, m, kk));
+  if (e != cudaSuccess) return fail(JTRLAN_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  TcWork w = tc_rotate_carve(base, n, m, kk);
+  int herr = 0;
+  e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_rotate_tc(V, n, m, Z, kk, out, w, true, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(base);
+  if (e != cudaSuccess) return fail(JTRLAN_ECUDA, std::string("tensor-core rotation: ") + cudaGetErrorString(e));
+  if (herr != 0)
+    return fail(JTRLAN_ETIMEOUT, "tensor-core rotation: a bounded wait ran out (code " + std::to_string(herr) + ")");
   return JTRLAN_OK;
 }
 

@@ -82,6 +82,22 @@ cudaError_t launch_shrink_df(void* V, const void* Vsrc, int64_t n, const int* pe
 cudaError_t launch_gather_pairs_df(const void* V, int64_t n, const int* order, int nev, int partners, void* out,
                                    cudaStream_t s);
 cudaError_t launch_rotate_df(const void* V, int64_t n, int m, const double* Z, int kk, void* Vout, cudaStream_t s);
+// Restart rotation of a (hi, lo) basis on the tensor cores (rotate_tc.cu): BF16 digit splitting of
+// both operands, exact FP32 accumulation of every digit pair, FP64 result as launch_rotate_df.
+struct TcWork {
+  int8_t* Erow = nullptr;   // 2n row exponents of V
+  uint8_t* Bimg = nullptr;  // BF16 digit planes of Z, ceil(kk_max/32) x ceil(m/16) x 7168 bytes
+  int* Ecol = nullptr;      // column exponents of Z
+  int* err = nullptr;       // nonzero: a bounded wait in the rotation kernel ran out
+  int64_t n = 0;
+  int m = 0, kk_max = 0;
+};
+int tc_rotate_max_m();
+size_t tc_rotate_bytes(int64_t n, int m, int kk_max);
+TcWork tc_rotate_carve(void* base, int64_t n, int m, int kk_max);
+// fresh_rowexp: recompute the row exponents of V (false: V is unchanged since the last call)
+cudaError_t launch_rotate_tc(const void* V, int64_t n, int m, const double* Z, int kk, void* out, const TcWork& w,
+                             bool fresh_rowexp, cudaStream_t s);
 // Stencil y (FP64) = A x with x and the links as (hi, lo) pairs; part (may be null) receives the
 // block partials of x^H y.  op.U / op.W: (hi, lo) links, structure-of-arrays [4][9][V].
 int matvec_df_blocks(const OpDev& op);

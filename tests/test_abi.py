@@ -49,10 +49,10 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_operator), offsetof(jtrlan_operator, n),
          offsetof(jtrlan_operator, m0), offsetof(jtrlan_operator, a11), offsetof(jtrlan_operator, W));
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_params), offsetof(jtrlan_params, tol),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_params), offsetof(jtrlan_params, tol),
          offsetof(jtrlan_params, v1), offsetof(jtrlan_params, check_jsym), offsetof(jtrlan_params, profile),
          offsetof(jtrlan_params, filter_hi), offsetof(jtrlan_params, filter_final_coeffs),
-         offsetof(jtrlan_params, plain_trlan));
+         offsetof(jtrlan_params, plain_trlan), offsetof(jtrlan_params, rotate_simt));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_stats), offsetof(jtrlan_stats, n_restarts),
          offsetof(jtrlan_stats, solve_ms), offsetof(jtrlan_stats, n_launches), offsetof(jtrlan_stats, n_ritz_fallbacks),
          offsetof(jtrlan_stats, n_matvec_fp32));
@@ -69,7 +69,8 @@ int main(void) {
     O, P, S, F = B.jtrlan_operator, B.jtrlan_params, B.jtrlan_stats, B.jtrlan_profile
     assert got[0] == [ctypes.sizeof(O), O.n.offset, O.m0.offset, O.a11.offset, O.W.offset]
     assert got[1] == [ctypes.sizeof(P), P.tol.offset, P.v1.offset, P.check_jsym.offset, P.profile.offset,
-                      P.filter_hi.offset, P.filter_final_coeffs.offset, P.plain_trlan.offset]
+                      P.filter_hi.offset, P.filter_final_coeffs.offset, P.plain_trlan.offset,
+                      P.rotate_simt.offset]
     assert got[2] == [ctypes.sizeof(S), S.n_restarts.offset, S.solve_ms.offset, S.n_launches.offset,
                       S.n_ritz_fallbacks.offset, S.n_matvec_fp32.offset]
     assert got[3] == [ctypes.sizeof(F), F.ms.offset, F.launches.offset, F.work.offset]
@@ -173,3 +174,15 @@ def test_batch_null_calls(lib):
     assert lib.jtrlan_batch_tune(None, None, None, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_batch_set_shape(None, 256, 0) == B.JTRLAN_EINVAL
     lib.jtrlan_batch_destroy(None)
+
+
+def test_rotate_df_rejects_bad_arguments_before_touching_the_device(lib):
+    # every check below fails on the host, so the dummy (never dereferenced) pointers are safe
+    d = ctypes.c_void_p(16)
+    assert lib.jtrlan_rotate_df(None, 10, 4, d, 2, d, 0, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_rotate_df(d, 0, 4, d, 2, d, 0, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_rotate_df(d, 10, 0, d, 2, d, 0, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_rotate_df(d, 10, 4, d, 0, d, 0, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_rotate_df(d, 10, 4, d, 2, d, 2, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_rotate_df(d, 10, 321, d, 2, d, 0, None) == B.JTRLAN_EINVAL   # tensor cores: m <= 320
+    assert "320" in lib.jtrlan_last_error().decode()
