@@ -192,6 +192,46 @@ def mixed_at_16(B, torch, stream, flush):
     return out
 
 
+# ---------------------------------------------------------------- invert mode (Algorithm 1, CG inner solves)
+def invert_compare(B, torch, stream, flush, op, w, t_normal, ev_normal, reps=3):
+    """Algorithm 1's invert mode on the headline workload: the same nev smallest pairs through
+    A^{-1} (conjugate gradients to 1e-12 per product), timed like the headline (one warm-up, then the
+    mean of `reps` solves, L2 flushed before each), against the normal-mode FP64 solve; and the paper's
+    invert-mode comparison of N_MV (A^{-1} applications) between TRLAN-JSYM and plain TRLAN, TRLAN run
+    with nev, m and mwin doubled to find both members of every pair."""
+    import ctypes
+    nev, m, mwin = w["nev"], w["m"], w["mwin"]
+    out = {"workload": "stencil_8x8x8x8", "nev": nev, "m": m, "mwin": mwin, "tol": TOL, "cg_tol": 1e-12}
+    ctx = B.jtrlan_create(op, B.params(nev, m, mwin, TOL, invert=1), stream.cuda_stream)
+    st = B.jtrlan_solve(ctx)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = B.jtrlan_solve(ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    ev = np.zeros(nev)
+    res = np.zeros(nev)
+    B.jtrlan_pairs(ctx, 0, ev.ctypes.data_as(ctypes.c_void_p), None, res.ctypes.data_as(ctypes.c_void_p))
+    B.jtrlan_destroy(ctx)
+    t = statistics.mean(ts)
+    out["jsym"] = {"value": t, "unit": "s", "n_matvec_inverse": st["n_matvec"], "n_cg_iters": st["n_cg_iters"],
+                   "n_matvec_inner": st["n_matvec_inner"], "n_restarts": st["n_restarts"],
+                   "max_residual": float(res.max()),
+                   "max_rel_eig_diff_vs_normal_mode": float(np.max(np.abs(ev - ev_normal) / np.abs(ev_normal))),
+                   "normal_mode_s": t_normal, "ratio_to_normal_mode": round(t / t_normal, 3)}
+    ctx = B.jtrlan_create(op, B.params(2 * nev, 2 * m, 2 * mwin, TOL, invert=1, plain_trlan=1), stream.cuda_stream)
+    st2 = B.jtrlan_solve(ctx)
+    B.jtrlan_destroy(ctx)
+    out["plain_trlan"] = {"n_matvec_inverse": st2["n_matvec"], "n_cg_iters": st2["n_cg_iters"],
+                          "n_restarts": st2["n_restarts"], "nev": 2 * nev, "m": 2 * m, "mwin": 2 * mwin}
+    out["n_matvec_ratio_trlan_over_jsym"] = round(st2["n_matvec"] / st["n_matvec"], 3)
+    return out
+
+
 # ---------------------------------------------------------------- FP32 stencil matvec vs HBM
 STENCIL_LATTICES = {"16x16x16x16": (16, 16, 16, 16), "24x24x24x48": (24, 24, 24, 48)}
 
@@ -653,6 +693,7 @@ def run_gb300(args, rank, world, local_rank):
                        "n_restarts": stm["n_restarts"],
                        "max_rel_eig_diff_vs_fp64": float(np.max(np.abs(evm - ev64) / np.abs(ev64))), "form": desc}
     mixed["chosen"] = min((k for k in forms), key=lambda k: mixed[k]["value"])
+    invert = invert_compare(B, torch, stream, flush, op, w, t_mean, ev64)
 
     # ---- one profiled solve per form: per-kernel device time
     def profiled(precision):
@@ -736,6 +777,7 @@ def run_gb300(args, rank, world, local_rank):
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "mixed": mixed, "stencil_matvec": stencil,
             "kernels": kernels,
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
+    line["invert_mode"] = invert
     line["stencil_fp32"] = {k: stencil_apply_roofline(v) for k, v in STENCIL_LATTICES.items()}
     line["rotate_tc"] = {k: rotate_roofline(v) for k, v in ROTATE_SHAPES.items()}
     if not args.no_learned:

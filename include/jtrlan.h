@@ -113,7 +113,16 @@ typedef struct {
  *     window, largest wanted, with FP64-accurate products; a Ritz vector x of B2 is accepted when
  *     ||A x - (x^H A x) x|| < tol (checked once B2's estimate is below 10 tol), and x^H A x is the
  *     eigenvalue reported.  Choose p2 strictly decreasing across the wanted eigenvalues: where p2 is
- *     flat, B2 cannot separate eigenvectors and the solve ends in JTRLAN_ENOCONV. */
+ *     flat, B2 cannot separate eigenvectors and the solve ends in JTRLAN_ENOCONV.
+ *   invert, cg_tol, cg_max_iter: Algorithm 1's invert mode, for the smallest eigenvalues of a
+ *     Hermitian positive definite J-symmetric A (Sec. 4 uses it with CG).  The Lanczos product is
+ *     A^{-1} v_j, each applied by conjugate gradients from x = 0 to ||v_j - A x|| <= cg_tol; the
+ *     wanted end is the largest eigenvalues lambda_i of T (those of A^{-1}); every restart takes
+ *     c = ||A v_{m+1}|| and reports ev(i) = 1/lambda_i with the residual estimate
+ *     res_est(i) = c |t_{m+1,i} ev(i)|, and the true residuals ||A v_i - ev(i) v_i|| use A itself.
+ *     Needs which = JTRLAN_SMALLEST, precision = JTRLAN_FP64 and no filter; plain_trlan may be set
+ *     (the TRLAN of the paper's comparison in invert mode).  A CG step with p^H A p <= 0 (A not
+ *     positive definite) ends the solve in JTRLAN_EBREAKDOWN. */
 typedef struct {
   int nev;
   int m;
@@ -135,6 +144,9 @@ typedef struct {
                          with W removed: Gram-Schmidt against V only) */
   int rotate_simt;    /* nonzero: the restart rotation of a compensated-FP32 basis runs on the CUDA
                          cores (jtrlan_rotate_df path 1) instead of the tensor cores */
+  int invert;         /* nonzero: Algorithm 1's invert mode (see below) */
+  double cg_tol;      /* invert mode: relative residual ||b - A x|| / ||b|| of each CG solve (0: 1e-12) */
+  int cg_max_iter;    /* invert mode: iterations per CG solve before JTRLAN_ENOCONV (0: 10000) */
 } jtrlan_params;
 
 /* Counters of the last solve (Sec. 3 counts only the Lanczos-step products as N_MV). */
@@ -149,6 +161,9 @@ typedef struct {
   int n_ritz_fallbacks;    /* restarts whose fast Ritz solve failed a check (Jacobi used) */
   int n_restarts_fp32;     /* JTRLAN_MIXED: outer iterations of the FP32 phase (in n_restarts) */
   int64_t n_matvec_fp32;   /* JTRLAN_MIXED: products of the FP32 phase (included in n_matvec) */
+  int64_t n_matvec_inner;  /* invert mode: products A p launched by the CG solves (N_MV counts the
+                              A^{-1} v_j), plus one A v_{m+1} per restart */
+  int64_t n_cg_iters;      /* invert mode: CG iterations to convergence, summed over the solves */
 } jtrlan_stats;
 
 /* Per-kernel-class profile of the last solve (filled when jtrlan_params.profile was set; the

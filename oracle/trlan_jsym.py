@@ -19,6 +19,10 @@ R7  The sort that moves converged pairs to the top is stable and acts on the fir
     nev positions; the final output is sorted by eigenvalue (ascending for
     'smallest', descending for 'largest').
 R9  v_1 = (1, ..., 1)/sqrt(n) as in Algorithm 1 unless a start vector is given.
+R20 Invert mode (Algorithm 1's second branch): the Lanczos product is A^{-1} v_j, given as the
+    function ``solve``; the wanted Ritz values of T are its largest (A's smallest); every restart
+    takes c = ||A v_{m+1}|| with v_{m+1} the last Lanczos vector, and ev(i) = 1/lambda_i,
+    res_est(i) = c |t_{m+1,i} ev(i)|.  The true residuals use A (``matvec``).
 """
 from __future__ import annotations
 
@@ -82,8 +86,9 @@ def lanczos_jsym(matvec, V, T, k, m, gamma=np.sqrt(2.0), gs_max_passes=3,
 
 
 def trlan_jsym(matvec, n, nev, m, mwin, tol, which="smallest", v1=None, max_restarts=1000,
-               gs_max_passes=3, on_lanczos=None, use_w=True):
-    """Algorithm 1 (TRLAN-JSYM), normal mode.
+               gs_max_passes=3, on_lanczos=None, use_w=True, solve=None):
+    """Algorithm 1 (TRLAN-JSYM), normal mode; invert mode when ``solve`` (b -> A^{-1} b) is given
+    (which must then be 'smallest', R20).
 
     Returns a dict with ``evals`` (nev,), ``X`` (n, nev), ``res`` (nev,), and the
     counters ``n_matvec`` (as counted in Sec. 3: the Lanczos-step products only),
@@ -93,6 +98,10 @@ def trlan_jsym(matvec, n, nev, m, mwin, tol, which="smallest", v1=None, max_rest
     """
     if n % 2 or not (0 < nev < m) or mwin < 0 or m >= n // 2:
         raise ValueError("need even n, 0 < nev < m < n/2 and mwin >= 0")
+    invert = solve is not None
+    if invert and which != "smallest":
+        raise ValueError("invert mode finds the smallest eigenvalues")
+    largest_of_T = (which == "largest") or invert
     V = np.zeros((n, m + 1), dtype=np.complex128)
     T = np.zeros((m + 1, m + 1))
     stats = dict(n_matvec=0, n_resid_matvec=0, n_gs_passes=0, n_restarts=0)
@@ -104,21 +113,28 @@ def trlan_jsym(matvec, n, nev, m, mwin, tol, which="smallest", v1=None, max_rest
     res_est = np.full(nev, np.inf)
     history = []
     for _ in range(max_restarts):
-        lanczos_jsym(matvec, V, T, k, m, gs_max_passes=gs_max_passes, stats=stats, use_w=use_w)
+        lanczos_jsym(solve if invert else matvec, V, T, k, m, gs_max_passes=gs_max_passes, stats=stats,
+                     use_w=use_w)
         stats["n_restarts"] += 1
         if on_lanczos is not None:
             on_lanczos(V, T, k, m)
         beta_m = T[m, m - 1]
         lam, Z = np.linalg.eigh(T[:m, :m])               # T_m = Z Lambda Z^T
-        order = np.argsort(lam if which == "smallest" else -lam, kind="stable")
+        order = np.argsort(-lam if largest_of_T else lam, kind="stable")
         lam, Z = lam[order], Z[:, order]                 # desired pairs first
         V[:, :m] = V[:, :m] @ Z                          # V_m := V_m Z_m
         T[:, :] = 0.0                                    # Krylov-Schur form of T-bar
         for i in range(m):
             T[i, i] = lam[i]
             T[m, i] = beta_m * Z[m - 1, i]               # t_{m+1,i} = t_{m+1,m} z_{m,i}
-        ev = lam[:nev].copy()
-        res_est = np.abs(T[m, :nev]).copy()
+        if invert:                                       # R20
+            c = np.linalg.norm(matvec(V[:, m]))          # c = ||A v_{m+1}||
+            stats["n_resid_matvec"] += 1
+            ev = 1.0 / lam[:nev]
+            res_est = c * np.abs(T[m, :nev] * ev)
+        else:
+            ev = lam[:nev].copy()
+            res_est = np.abs(T[m, :nev]).copy()
         is_convd = np.zeros(nev, dtype=bool)             # R6
         for i in range(nev):
             if res_est[i] < tol:                         # check the true residual

@@ -46,7 +46,8 @@ class jtrlan_params(ctypes.Structure):
                 ("filter_degree", ctypes.c_int), ("filter_coeffs", ctypes.c_void_p), ("filter_lo", ctypes.c_double),
                 ("filter_hi", ctypes.c_double), ("filter_final_degree", ctypes.c_int),
                 ("filter_final_coeffs", ctypes.c_void_p), ("plain_trlan", ctypes.c_int),
-                ("rotate_simt", ctypes.c_int)]
+                ("rotate_simt", ctypes.c_int), ("invert", ctypes.c_int), ("cg_tol", ctypes.c_double),
+                ("cg_max_iter", ctypes.c_int)]
 
 
 class jtrlan_stats(ctypes.Structure):
@@ -54,7 +55,8 @@ class jtrlan_stats(ctypes.Structure):
                 ("n_gs_passes", ctypes.c_int64), ("n_restarts", ctypes.c_int),
                 ("icnv", ctypes.c_int), ("solve_ms", ctypes.c_double), ("n_launches", ctypes.c_int64),
                 ("n_ritz_fallbacks", ctypes.c_int), ("n_restarts_fp32", ctypes.c_int),
-                ("n_matvec_fp32", ctypes.c_int64)]
+                ("n_matvec_fp32", ctypes.c_int64), ("n_matvec_inner", ctypes.c_int64),
+                ("n_cg_iters", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -339,7 +341,8 @@ def dense_operator(n, a11_ptr, a12_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
 
 def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_restarts=0,
            gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0, filter_coeffs=None, filter_window=None,
-           filter_final_coeffs=None, plain_trlan=0, rotate_simt=0) -> jtrlan_params:
+           filter_final_coeffs=None, plain_trlan=0, rotate_simt=0, invert=0, cg_tol=0.0,
+           cg_max_iter=0) -> jtrlan_params:
     """filter_coeffs / filter_final_coeffs: float64 arrays g_0..g_d (kept alive on the struct until
     create copies them); filter_window: (lo, hi)."""
     p = jtrlan_params()
@@ -351,6 +354,7 @@ def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_
     p.profile = int(profile)
     p.plain_trlan = int(plain_trlan)
     p.rotate_simt = int(rotate_simt)
+    p.invert, p.cg_tol, p.cg_max_iter = int(invert), float(cg_tol), int(cg_max_iter)
     if filter_coeffs is not None:
         import numpy as np
         g = np.ascontiguousarray(filter_coeffs, dtype=np.float64)

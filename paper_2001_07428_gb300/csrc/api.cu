@@ -45,7 +45,7 @@ __global__ void c64_to_c128_kernel(const float2* in, double2* out, int64_t count
 }
 
 const char* kTagNames[K_NTAGS] = {"matvec", "gs_first", "gs_reduce", "gs_update", "gs_dot", "gs_normalize",
-                                  "ritz", "rotate", "resid", "shrink", "other", "ritz_fallback", "filter", "gs_step"};
+                                  "ritz", "rotate", "resid", "shrink", "other", "ritz_fallback", "filter", "gs_step", "cg"};
 
 // Optional per-launch CUDA-event timing, harvested at the host synchronisation points.
 struct Profiler {
@@ -153,6 +153,13 @@ struct jtrlan_ctx {
   int gs_nblk = 0, gs_rpb = 0;
   int coop64 = 0, coop32 = 0, coopdf = 0;   // row blocks (= CTAs) of the cooperative Gram-Schmidt step; 0: not used
   int coop_rpb = 0, coop_rpb_df = 0;        // its rows per block
+  bool invert = false;             // Algorithm 1's invert mode: the Lanczos product is A^{-1} v by CG
+  void *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;   // CG residual, direction, A p
+  double* cg_part = nullptr;       // cg_blocks(n) partials
+  double* cg_pq = nullptr;         // product partials of p^H A p (double2)
+  CgState* cg_st = nullptr;
+  CgState* h_cgst = nullptr;       // pinned copy
+  int64_t cg_matvecs = 0, cg_iters = 0;
   TcWork tc{};                     // scratch of the tensor-core rotation (compensated-FP32 basis)
   bool tc_on = false;
   int* h_tcerr = nullptr;          // pinned copy of its error flag
@@ -256,6 +263,12 @@ jtrlan_status validate(const jtrlan_operator* op, const jtrlan_params* p) {
   if (p->filter_final_degree > 0 && !p->filter_final_coeffs) return fail(JTRLAN_EINVAL, "null filter_final_coeffs");
   if ((p->filter_degree > 0 || p->filter_final_degree > 0) && !(p->filter_lo < p->filter_hi))
     return fail(JTRLAN_EINVAL, "need filter_lo < filter_hi");
+  if (p->invert) {
+    if (p->precision != JTRLAN_FP64) return fail(JTRLAN_EINVAL, "invert mode runs in JTRLAN_FP64");
+    if (p->which != JTRLAN_SMALLEST) return fail(JTRLAN_EINVAL, "invert mode finds the smallest eigenvalues");
+    if (p->filter_degree > 0 || p->filter_final_degree > 0) return fail(JTRLAN_EINVAL, "invert mode takes no filter");
+  }
+  if (p->cg_tol < 0.0 || p->cg_max_iter < 0) return fail(JTRLAN_EINVAL, "need cg_tol >= 0 and cg_max_iter >= 0");
   return JTRLAN_OK;
 }
 
@@ -374,6 +387,22 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   }
   c->p64.which = c->pdf.which = prm->which;
   if (!c->p32.filtered) c->p32.which = prm->which;
+  if (prm->invert) {   // Lanczos on A^{-1}: its largest eigenvalues are A's smallest
+    c->invert = true;
+    c->p64.which = JTRLAN_LARGEST;
+    JT_TRY(c->dalloc(&c->cg_r, (size_t)c->n * sizeof(double2)));
+    JT_TRY(c->dalloc(&c->cg_p, (size_t)c->n * sizeof(double2)));
+    JT_TRY(c->dalloc(&c->cg_q, (size_t)c->n * sizeof(double2)));
+    JT_TRY(c->dalloc(&c->cg_part, (size_t)cg_blocks(c->n) * sizeof(double)));
+    JT_TRY(c->dalloc(&c->cg_pq, (size_t)c->p64.mv_nblk * sizeof(double2)));
+    JT_TRY(c->dalloc(&c->cg_st, sizeof(CgState)));
+    JT_TRY(c->halloc(&c->h_cgst, sizeof(CgState)));
+    JT_CUDA(cudaMemsetAsync(c->cg_st, 0, sizeof(CgState), c->stream));
+    if (cg_blocks(c->n) > c->p64.mv_nblk)
+      JT_TRY(c->dalloc(&c->p64.alpha_part, (size_t)cg_blocks(c->n) * sizeof(double2)));
+    if (cg_blocks(c->n) > c->p64.mv_nblk * c->nev)
+      JT_TRY(c->dalloc(&c->p64.resid_part, (size_t)cg_blocks(c->n) * sizeof(double)));
+  }
   c->fc = 0.5 * (prm->filter_lo + prm->filter_hi);
   c->fe = 0.5 * (prm->filter_hi - prm->filter_lo);
   if (prm->filter_final_degree > 0) {   // the certifying phase on B = p(A), judged by A's residuals
@@ -578,6 +607,40 @@ jtrlan_status rq_resid(jtrlan_ctx* c, Phase& ph, const void* x, double* lam_out,
   return JTRLAN_OK;
 }
 
+// y = A^{-1} b by conjugate gradients (cg.cu) on the FP64 operator, for the invert mode: iterations
+// are enqueued in groups of kCgGroup, and the host reads the device state after each group.
+constexpr int kCgGroup = 4;
+jtrlan_status cg_solve(jtrlan_ctx* c, Phase& ph, const void* b, void* y) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  const double rtol = c->prm.cg_tol > 0.0 ? c->prm.cg_tol : 1e-12;
+  const int max_iter = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : 10000;
+  LAUNCH(K_CG, launch_cg_init(b, y, c->cg_r, c->cg_p, n, c->cg_part, rtol, c->cg_st, s));
+  c->nl[K_CG] += 1;   // two kernels
+  for (int launched = 0;;) {
+    for (int u = 0; u < kCgGroup; ++u) {
+      LAUNCH(K_CG, launch_matvec<double>(ph.op, (const double2*)c->cg_p, (double2*)c->cg_q, MV_ALPHA, c->cg_pq,
+                                         nullptr, nullptr, 0, 0, nullptr, s));
+      LAUNCH(K_CG, launch_cg_alpha(c->cg_pq, ph.mv_nblk, c->cg_st, s));
+      LAUNCH(K_CG, launch_cg_update(y, c->cg_r, c->cg_p, c->cg_q, n, c->cg_part, c->cg_st, s));
+      c->nl[K_CG] += 2;   // three kernels
+    }
+    launched += kCgGroup;
+    c->cg_matvecs += kCgGroup;
+    c->work[K_CG] += (double)kCgGroup * (c->opd.kind == JTRLAN_STENCIL4D ? (double)ph.op.vol : (double)c->h * c->h);
+    JT_CUDA(cudaMemcpyAsync(c->h_cgst, c->cg_st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    JT_CUDA(cudaStreamSynchronize(s));
+    if (c->h_cgst->fail)
+      return fail(JTRLAN_EBREAKDOWN, "invert mode: a CG step found p^H A p <= 0 (A is not positive definite)");
+    if (c->h_cgst->done) {
+      c->cg_iters += c->h_cgst->iters;
+      return JTRLAN_OK;
+    }
+    if (launched >= max_iter)
+      return fail(JTRLAN_ENOCONV, "invert mode: CG did not reach cg_tol in cg_max_iter iterations");
+  }
+}
+
 // Algorithm 2 steps j0 .. j1-1 of the phase (products, alpha, Gram-Schmidt against V and W with the
 // sqrt(2) test, normalisation), enqueued without host synchronisation.  With `filtered` the product
 // is B = p(A).
@@ -588,7 +651,8 @@ jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1,
   const int64_t n = c->n;
   const size_t cs = ph.cs;
   if (ph.df) LAUNCH(K_OTHER, launch_fp64_from_df(col(ph.V, n, j0, cs), ph.x, n, s));   // v_j0 in FP64
-  const int mv_parts = (filtered && !(ph.certify && ph.dfmv)) ? cheb_blocks(n)
+  const int mv_parts = c->invert ? cg_blocks(n)
+                       : (filtered && !(ph.certify && ph.dfmv)) ? cheb_blocks(n)
                        : ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk;
   for (int j = j0; j < j1; ++j) {
     if (filtered) {
@@ -598,6 +662,9 @@ jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1,
         JT_TRY(filter_apply_cert(c, ph, j));
     } else if (ph.dfmv) {   // compensated FP32 on the (hi, lo) column and links, FP64 result
       LAUNCH(K_MATVEC, launch_matvec_df(ph.opdf, col(ph.V, n, j, cs), ph.y, ph.alpha_part, s));
+    } else if (c->invert) {   // invert mode: y = A^{-1} v_j by CG, then the partials of v_j^H y
+      JT_TRY(cg_solve(c, ph, col(ph.V, n, j, cs), ph.y));
+      LAUNCH(K_CG, launch_vhy_part(col(ph.V, n, j, cs), ph.y, n, ph.alpha_part, s));
     } else {
       const void* vj = ph.df ? ph.x : col(ph.V, n, j, cs);
       LAUNCH(K_MATVEC, launch_matvec<R>(ph.op, (const C*)vj, (C*)ph.y, MV_ALPHA, ph.alpha_part,
@@ -680,8 +747,17 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     // ---- Algorithm 2: m - k Lanczos steps, no host synchronisation inside
     JT_TRY(lanczos_steps<R>(c, ph, a, k, m, ph.filtered));
     const int per_step = ph.filtered ? (int)ph.fcoef.size() - 1 : 1;   // products of A per Lanczos step
-    stt.n_matvec += (int64_t)(m - k) * per_step;
-    c->work[K_MATVEC] += (double)(m - k) * per_step * mv_units;
+    stt.n_matvec += (int64_t)(m - k) * per_step;                         // invert mode: A^{-1} v_j
+    if (!c->invert) c->work[K_MATVEC] += (double)(m - k) * per_step * mv_units;
+    if (c->invert) {   // c = ||A v_{m+1}|| of the invert-mode residual estimates (Algorithm 1)
+      const void* vm1 = col(ph.V, n, m, cs);
+      LAUNCH(K_CG, launch_matvec<double>(ph.op, (const double2*)vm1, (double2*)c->cg_q, MV_PLAIN, nullptr, nullptr,
+                                         nullptr, 0, 0, nullptr, s));
+      LAUNCH(K_CG, launch_resid_part(c->cg_q, vm1, &c->cg_st->zero, n, ph.resid_part, s));
+      LAUNCH(K_CG, launch_reduce_norms(ph.resid_part, cheb_blocks(n), 1, &c->cg_st->cnorm, s));
+      c->cg_matvecs += 1;
+      c->work[K_CG] += mv_units;
+    }
     stt.n_restarts += 1;
     // ---- Rayleigh-Ritz (FP64): T_m = Z Lambda Z^T, the kk wanted pairs; V_m Z into Vtmp
     LAUNCH(K_RITZ, launch_ritz(c->T, ldt, m, k, kk, ph.which, c->lam, c->Z, c->ritz_flags, s));
@@ -707,6 +783,7 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     LAUNCH(K_OTHER, launch_report(c->lam, c->Z, m, c->T, ldt, c->st, c->d_rep, s));
     JT_CUDA(cudaMemcpyAsync(c->h_rep, c->d_rep, (size_t)(2 * m + 8) * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (ph.df && c->tc_on) JT_CUDA(cudaMemcpyAsync(c->h_tcerr, c->tc.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (c->invert) JT_CUDA(cudaMemcpyAsync(c->h_cgst, c->cg_st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     JT_CUDA(cudaStreamSynchronize(s));
     JT_CUDA(c->prof.harvest());
     if (ph.df && c->tc_on && *c->h_tcerr != 0)
@@ -729,9 +806,11 @@ jtrlan_status run_phase(jtrlan_ctx* c, Phase& ph, double tol, double tol_rel_tma
     }
     int ncand = 0;
     std::vector<char> reused(nev, 0);
+    const double cnorm = c->invert ? c->h_cgst->cnorm : 0.0;
     for (int i = 0; i < nev; ++i) {
-      ev[i] = lamv[i];
-      res_est[i] = std::fabs(arrow[i]);
+      // invert mode: T holds A^{-1}'s Ritz values; ev(i) = 1/lambda_i, res_est(i) = c |t_{m+1,i} ev(i)|
+      ev[i] = c->invert ? 1.0 / lamv[i] : lamv[i];
+      res_est[i] = c->invert ? cnorm * std::fabs(arrow[i] * ev[i]) : std::fabs(arrow[i]);
       conv[i] = 0;                            // is_convd reset every outer iteration
       // a certifying filtered phase tests A's residual once B's estimate is near tol (B = p(A)
       // scales residuals by about |p'(lambda)|, so the estimate alone is neither necessary nor enough)
@@ -903,6 +982,7 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
   for (int t = 0; t < K_NTAGS; ++t) { c->prof.ms[t] = 0; c->nl[t] = 0; c->work[t] = 0; }
   for (int t = 0; t < 3; ++t) c->work_base[t] = 0;
   c->fallback_base = 0;
+  c->cg_matvecs = c->cg_iters = 0;
   c->gs_pass_base = 0;
   std::vector<double> ev, res;
   int icnv = 0;
@@ -958,6 +1038,8 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
   stt.n_restarts += s64.n_restarts;
   stt.n_ritz_fallbacks = s64.n_ritz_fallbacks;
   stt.icnv = icnv;
+  stt.n_matvec_inner = c->cg_matvecs;
+  stt.n_cg_iters = c->cg_iters;
   for (int t = 0; t < K_NTAGS; ++t) stt.n_launches += c->nl[t];
   stt.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   c->stats = stt;

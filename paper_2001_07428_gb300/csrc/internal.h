@@ -82,6 +82,25 @@ cudaError_t launch_shrink_df(void* V, const void* Vsrc, int64_t n, const int* pe
 cudaError_t launch_gather_pairs_df(const void* V, int64_t n, const int* order, int nev, int partners, void* out,
                                    cudaStream_t s);
 cudaError_t launch_rotate_df(const void* V, int64_t n, int m, const double* Z, int kk, void* Vout, cudaStream_t s);
+// Conjugate gradients for the invert mode (cg.cu): y = A^{-1} b for Hermitian positive definite A.
+struct CgState {
+  double rr, rr0, alpha, beta, tol2;   // r^H r, |b|^2, the step scalars, (rtol |b|)^2
+  int done, iters, fail;               // converged (or failed); iterations; p^H A p <= 0 seen
+  double cnorm;                        // ||A v_{m+1}|| of the invert-mode residual estimate
+  double zero;                         // 0.0, the lambda of a plain norm through launch_resid_part
+};
+int cg_blocks(int64_t n);
+// x = 0, r = p = b, and the state from |b|^2 (cg_blocks(n) partials in part)
+cudaError_t launch_cg_init(const void* b, void* x, void* r, void* p, int64_t n, double* part, double rtol, CgState* st,
+                           cudaStream_t s);
+// alpha from the partials of p^H (A p) that launch_matvec(MV_ALPHA) left for p
+cudaError_t launch_cg_alpha(const double* pq_part, int nblk, CgState* st, cudaStream_t s);
+// x += alpha p, r -= alpha q, beta and the convergence test, p = r + beta p
+cudaError_t launch_cg_update(void* x, void* r, void* p, const void* q, int64_t n, double* part, CgState* st,
+                             cudaStream_t s);
+// cg_blocks(n) partials (double2) of v^H y
+cudaError_t launch_vhy_part(const void* v, const void* y, int64_t n, double* part, cudaStream_t s);
+
 // Restart rotation of a (hi, lo) basis on the tensor cores (rotate_tc.cu): BF16 digit splitting of
 // both operands, exact FP32 accumulation of every digit pair, FP64 result as launch_rotate_df.
 struct TcWork {
@@ -114,7 +133,7 @@ cudaError_t launch_links_df(const void* in, void* out, int64_t vol, cudaStream_t
 // Kernel classes for the optional per-kernel profile.
 enum KernelTag {
   K_MATVEC = 0, K_GS_FIRST, K_GS_REDUCE, K_GS_UPDATE, K_GS_DOT, K_GS_NORMALIZE, K_RITZ, K_ROTATE,
-  K_RESID, K_SHRINK, K_OTHER, K_RITZ_FALLBACK, K_FILTER, K_GS_STEP, K_NTAGS
+  K_RESID, K_SHRINK, K_OTHER, K_RITZ_FALLBACK, K_FILTER, K_GS_STEP, K_CG, K_NTAGS
 };
 template <typename R>
 cudaError_t launch_fill_ones(void* v, int64_t n, cudaStream_t s);

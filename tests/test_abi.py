@@ -49,13 +49,15 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_operator), offsetof(jtrlan_operator, n),
          offsetof(jtrlan_operator, m0), offsetof(jtrlan_operator, a11), offsetof(jtrlan_operator, W));
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_params), offsetof(jtrlan_params, tol),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_params), offsetof(jtrlan_params, tol),
          offsetof(jtrlan_params, v1), offsetof(jtrlan_params, check_jsym), offsetof(jtrlan_params, profile),
          offsetof(jtrlan_params, filter_hi), offsetof(jtrlan_params, filter_final_coeffs),
-         offsetof(jtrlan_params, plain_trlan), offsetof(jtrlan_params, rotate_simt));
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_stats), offsetof(jtrlan_stats, n_restarts),
+         offsetof(jtrlan_params, plain_trlan), offsetof(jtrlan_params, rotate_simt),
+         offsetof(jtrlan_params, invert), offsetof(jtrlan_params, cg_tol), offsetof(jtrlan_params, cg_max_iter));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_stats), offsetof(jtrlan_stats, n_restarts),
          offsetof(jtrlan_stats, solve_ms), offsetof(jtrlan_stats, n_launches), offsetof(jtrlan_stats, n_ritz_fallbacks),
-         offsetof(jtrlan_stats, n_matvec_fp32));
+         offsetof(jtrlan_stats, n_matvec_fp32), offsetof(jtrlan_stats, n_matvec_inner),
+         offsetof(jtrlan_stats, n_cg_iters));
   printf("%zu %zu %zu %zu\n", sizeof(jtrlan_profile), offsetof(jtrlan_profile, ms),
          offsetof(jtrlan_profile, launches), offsetof(jtrlan_profile, work));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_batch_stats), offsetof(jtrlan_batch_stats, n_matvec),
@@ -70,9 +72,10 @@ int main(void) {
     assert got[0] == [ctypes.sizeof(O), O.n.offset, O.m0.offset, O.a11.offset, O.W.offset]
     assert got[1] == [ctypes.sizeof(P), P.tol.offset, P.v1.offset, P.check_jsym.offset, P.profile.offset,
                       P.filter_hi.offset, P.filter_final_coeffs.offset, P.plain_trlan.offset,
-                      P.rotate_simt.offset]
+                      P.rotate_simt.offset, P.invert.offset, P.cg_tol.offset, P.cg_max_iter.offset]
     assert got[2] == [ctypes.sizeof(S), S.n_restarts.offset, S.solve_ms.offset, S.n_launches.offset,
-                      S.n_ritz_fallbacks.offset, S.n_matvec_fp32.offset]
+                      S.n_ritz_fallbacks.offset, S.n_matvec_fp32.offset, S.n_matvec_inner.offset,
+                      S.n_cg_iters.offset]
     assert got[3] == [ctypes.sizeof(F), F.ms.offset, F.launches.offset, F.work.offset]
     Q = B.jtrlan_batch_stats
     assert got[4] == [ctypes.sizeof(Q), Q.n_matvec.offset, Q.max_restarts.offset, Q.graph.offset,
@@ -186,3 +189,24 @@ def test_rotate_df_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.jtrlan_rotate_df(d, 10, 4, d, 2, d, 2, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_rotate_df(d, 10, 321, d, 2, d, 0, None) == B.JTRLAN_EINVAL   # tensor cores: m <= 320
     assert "320" in lib.jtrlan_last_error().decode()
+
+
+def test_invert_mode_parameter_checks(lib):
+    # invert mode needs FP64, the smallest end and no filter; all rejected before any device work
+    import numpy as np
+    n = 12
+    a = ctypes.c_void_p(16)
+    op = B.dense_operator(n, a, a)
+    for kw in (dict(precision=B.JTRLAN_MIXED_REORTH), dict(which=B.JTRLAN_LARGEST), dict(cg_tol=-1.0),
+               dict(cg_max_iter=-3)):
+        args = dict(which=B.JTRLAN_SMALLEST, precision=B.JTRLAN_FP64)
+        args.update(kw)
+        prm = B.params(2, 4, 1, 1e-8, invert=1, **args)
+        with pytest.raises(B.JTRLanError) as ei:
+            B.jtrlan_create(op, prm, 0)
+        assert ei.value.status == B.JTRLAN_EINVAL
+    prm = B.params(2, 4, 1, 1e-8, invert=1, filter_final_coeffs=np.ones(3), filter_window=(0.0, 1.0))
+    prm.filter_final_degree = 2
+    with pytest.raises(B.JTRLanError) as ei:
+        B.jtrlan_create(op, prm, 0)
+    assert ei.value.status == B.JTRLAN_EINVAL
