@@ -75,7 +75,45 @@ __device__ void dfdot_body(const GSArgs& a, int64_t p0, int64_t p1, const float4
 #pragma unroll
       for (int t = 0; t < 4; ++t) s[c][t] = e[c][t] = 0.f;
     const int ncol = min(kCols, a.j + 1 - c0);
-    for (int64_t r = lane; r < rows; r += 32) {
+    // four rows per lane: their eight loads of V are issued before the arithmetic, so a warp keeps
+    // 4 KB in flight (the basis is read from HBM once per pass and the y tile sits in shared memory)
+    int64_t r0 = lane;
+    for (; r0 + 96 < rows; r0 += 128) {
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) {
+        if (c < ncol) {
+          const float4* vi = V + (int64_t)(c0 + c) * n + p0;
+          float4 v1u[4], v2u[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            v1u[u] = vi[r0 + 32 * u];
+            v2u[u] = vi[h + r0 + 32 * u];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 y1 = ys[r0 + 32 * u], y2 = ys[rows + r0 + 32 * u];
+            const float4 v1 = v1u[u], v2 = v2u[u];
+            df_acc(s[c][0], e[c][0], v1.x, v1.z, y1.x, y1.z);
+            df_acc(s[c][0], e[c][0], v1.y, v1.w, y1.y, y1.w);
+            df_acc(s[c][0], e[c][0], v2.x, v2.z, y2.x, y2.z);
+            df_acc(s[c][0], e[c][0], v2.y, v2.w, y2.y, y2.w);
+            df_acc(s[c][1], e[c][1], v1.x, v1.z, y1.y, y1.w);
+            df_sub(s[c][1], e[c][1], v1.y, v1.w, y1.x, y1.z);
+            df_acc(s[c][1], e[c][1], v2.x, v2.z, y2.y, y2.w);
+            df_sub(s[c][1], e[c][1], v2.y, v2.w, y2.x, y2.z);
+            df_acc(s[c][2], e[c][2], v1.x, v1.z, y2.x, y2.z);
+            df_sub(s[c][2], e[c][2], v1.y, v1.w, y2.y, y2.w);
+            df_sub(s[c][2], e[c][2], v2.x, v2.z, y1.x, y1.z);
+            df_acc(s[c][2], e[c][2], v2.y, v2.w, y1.y, y1.w);
+            df_acc(s[c][3], e[c][3], v1.x, v1.z, y2.y, y2.w);
+            df_acc(s[c][3], e[c][3], v1.y, v1.w, y2.x, y2.z);
+            df_sub(s[c][3], e[c][3], v2.x, v2.z, y1.y, y1.w);
+            df_sub(s[c][3], e[c][3], v2.y, v2.w, y1.x, y1.z);
+          }
+        }
+      }
+    }
+    for (int64_t r = r0; r < rows; r += 32) {
       const float4 y1 = ys[r], y2 = ys[rows + r];
       const int64_t p = p0 + r;
 #pragma unroll
@@ -221,129 +259,77 @@ __global__ void __launch_bounds__(kThreads, kDotMinBlocks) gsdf_dot_kernel(GSArg
   dfdot_body(a, p0, p1, ys, red, blockIdx.x);
 }
 
-// y -= V c_v + W c_w: the correction is accumulated per row in compensated FP32 over this warp's
-// columns, the eight warps' pieces are added in FP64, and y is updated in FP64.
-__global__ void __launch_bounds__(kThreads) gsdf_update_kernel(GSArgs a) {
-  extern __shared__ float4 scf[];                       // per column: {cv hi/lo}, {cw hi/lo}
-  __shared__ float red_s[kGroups][32][4], red_e[kGroups][32][4];
-  __shared__ double sh[32];
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = a.st->done;
-  __syncthreads();
-  if (s_skip) return;
-  const int j = a.j;
-  for (int i = threadIdx.x; i <= j; i += kThreads) {
-    const coef4 c = a.coef[i];
-    scf[2 * i] = split(make_double2(c.vr, c.vi));
-    scf[2 * i + 1] = split(make_double2(c.wr, c.wi));
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.st->units_update += (double)(j + 1) * (double)a.h;
-  __syncthreads();
+// y -= V c_v + W c_w over rows [p0, p1): warp q owns rows p0 + 32 q + lane, then + 256, ...; every
+// column is accumulated per row in compensated FP32 (four columns' loads in flight), converted once
+// and applied to y in FP64 by the warp that owns the row: no cross-warp reduction and no barrier.
+// Returns this thread's share of ||y||^2.  The branch depends only on the block's row range, so it is
+// uniform across the block (dfupdate_split has barriers).
+// Blocks with fewer than 256 rows (the small lattices' cooperative partition) take dfupdate_split
+// instead, so that no warp idles.
+__device__ double dfupdate_split(const GSArgs& a, int64_t p0, int64_t p1, const float4* scf, float (*red_s)[32][4],
+                                 float (*red_e)[32][4]);
+__device__ double dfupdate_rows(const GSArgs& a, int64_t p0, int64_t p1, const float4* scf, float (*red_s)[32][4],
+                                float (*red_e)[32][4]) {
+  if (p1 - p0 < 32 * kGroups) return dfupdate_split(a, p0, p1, scf, red_s, red_e);
   const float4* V = (const float4*)a.V;
   double2* y = (double2*)a.y;
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   const int64_t n = a.n, h = a.h;
-  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
-  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+  const int j = a.j;
   double nrm = 0.0;
-  for (int64_t pb = p0; pb < p1; pb += 32) {
-    const int64_t p = pb + lane;
-    const bool ok = p < p1;
+  for (int64_t p = p0 + 32 * q + lane; p < p1; p += 32 * kGroups) {
     float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
-    if (ok) {
-      for (int i = q; i <= j; i += kGroups) {
-        const float4 v1 = V[(int64_t)i * n + p], v2 = V[(int64_t)i * n + h + p];
-        const float4 cv = scf[2 * i], cw = scf[2 * i + 1];
-        // y1 correction: v1 c_v - conj(v2) c_w
+    int i = 0;
+    for (; i + 3 <= j; i += 4) {
+      float4 v1u[4], v2u[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v1u[u] = V[(int64_t)(i + u) * n + p];
+        v2u[u] = V[(int64_t)(i + u) * n + h + p];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 v1 = v1u[u], v2 = v2u[u];
+        const float4 cv = scf[2 * (i + u)], cw = scf[2 * (i + u) + 1];
+        // y1 correction: v1 c_v - conj(v2) c_w;  y2 correction: v2 c_v + conj(v1) c_w
         df_acc(s[0], e[0], v1.x, v1.z, cv.x, cv.z);  df_sub(s[0], e[0], v1.y, v1.w, cv.y, cv.w);
         df_sub(s[0], e[0], v2.x, v2.z, cw.x, cw.z);  df_sub(s[0], e[0], v2.y, v2.w, cw.y, cw.w);
         df_acc(s[1], e[1], v1.x, v1.z, cv.y, cv.w);  df_acc(s[1], e[1], v1.y, v1.w, cv.x, cv.z);
         df_sub(s[1], e[1], v2.x, v2.z, cw.y, cw.w);  df_acc(s[1], e[1], v2.y, v2.w, cw.x, cw.z);
-        // y2 correction: v2 c_v + conj(v1) c_w
         df_acc(s[2], e[2], v2.x, v2.z, cv.x, cv.z);  df_sub(s[2], e[2], v2.y, v2.w, cv.y, cv.w);
         df_acc(s[2], e[2], v1.x, v1.z, cw.x, cw.z);  df_acc(s[2], e[2], v1.y, v1.w, cw.y, cw.w);
         df_acc(s[3], e[3], v2.x, v2.z, cv.y, cv.w);  df_acc(s[3], e[3], v2.y, v2.w, cv.x, cv.z);
         df_acc(s[3], e[3], v1.x, v1.z, cw.y, cw.w);  df_sub(s[3], e[3], v1.y, v1.w, cw.x, cw.z);
       }
     }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      red_s[q][lane][t] = s[t];
-      red_e[q][lane][t] = e[t];
+    for (; i <= j; ++i) {
+      const float4 v1 = V[(int64_t)i * n + p], v2 = V[(int64_t)i * n + h + p];
+      const float4 cv = scf[2 * i], cw = scf[2 * i + 1];
+      df_acc(s[0], e[0], v1.x, v1.z, cv.x, cv.z);  df_sub(s[0], e[0], v1.y, v1.w, cv.y, cv.w);
+      df_sub(s[0], e[0], v2.x, v2.z, cw.x, cw.z);  df_sub(s[0], e[0], v2.y, v2.w, cw.y, cw.w);
+      df_acc(s[1], e[1], v1.x, v1.z, cv.y, cv.w);  df_acc(s[1], e[1], v1.y, v1.w, cv.x, cv.z);
+      df_sub(s[1], e[1], v2.x, v2.z, cw.y, cw.w);  df_acc(s[1], e[1], v2.y, v2.w, cw.x, cw.z);
+      df_acc(s[2], e[2], v2.x, v2.z, cv.x, cv.z);  df_sub(s[2], e[2], v2.y, v2.w, cv.y, cv.w);
+      df_acc(s[2], e[2], v1.x, v1.z, cw.x, cw.z);  df_acc(s[2], e[2], v1.y, v1.w, cw.y, cw.w);
+      df_acc(s[3], e[3], v2.x, v2.z, cv.y, cv.w);  df_acc(s[3], e[3], v2.y, v2.w, cv.x, cv.z);
+      df_acc(s[3], e[3], v1.x, v1.z, cw.y, cw.w);  df_sub(s[3], e[3], v1.y, v1.w, cw.x, cw.z);
     }
-    __syncthreads();
-    if (q == 0 && ok) {
-      double c[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {   // the eight column groups, still compensated; one conversion
-        float S = red_s[0][lane][t], E = red_e[0][lane][t];
-#pragma unroll
-        for (int g = 1; g < kGroups; ++g) {
-          float u, ue;
-          two_sum(S, red_s[g][lane][t], u, ue);
-          S = u;
-          E = __fadd_rn(E, __fadd_rn(ue, red_e[g][lane][t]));
-        }
-        c[t] = (double)S + (double)E;
-      }
-      double2 y1 = y[p], y2 = y[h + p];
-      y1.x -= c[0]; y1.y -= c[1];
-      y2.x -= c[2]; y2.y -= c[3];
-      y[p] = y1;
-      y[h + p] = y2;
-      nrm += cabs2(y1) + cabs2(y2);
-    }
-    __syncthreads();
+    double2 y1 = y[p], y2 = y[h + p];
+    y1.x -= (double)s[0] + (double)e[0];
+    y1.y -= (double)s[1] + (double)e[1];
+    y2.x -= (double)s[2] + (double)e[2];
+    y2.y -= (double)s[3] + (double)e[3];
+    y[p] = y1;
+    y[h + p] = y2;
+    nrm += cabs2(y1) + cabs2(y2);
   }
-  nrm = block_sum(nrm, sh);
-  if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
+  return nrm;
 }
 
-// v_{j+1} = y / beta stored split into V4[:, j+1] and in FP64 into x (the next matvec input).
-__global__ void __launch_bounds__(kThreads) gsdf_normalize_kernel(GSArgs a, double2* __restrict__ x) {
-  __shared__ double sh[32];
-  StepState* st = a.st;
-  const int done = st->done;
-  double beta;
-  if (done) {
-    beta = st->beta;
-  } else {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < a.nblk; b += kThreads) s += a.part_nrm[b];
-    beta = sqrt(block_sum(s, sh));
-  }
-  const double tmax = st->tmax;
-  const bool brk = !(beta > 1e-14 * fmax(tmax, 1.0));
-  const double inv = brk ? 0.0 : 1.0 / beta;
-  const double2* y = (const double2*)a.y;
-  float4* v = (float4*)a.V + (int64_t)(a.j + 1) * a.n;
-  const int64_t h = a.h;
-  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
-  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
-  for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
-    const double2 y1 = y[p], y2 = y[h + p];
-    const double2 v1 = make_double2(y1.x * inv, y1.y * inv), v2 = make_double2(y2.x * inv, y2.y * inv);
-    v[p] = split(v1);
-    v[h + p] = split(v2);
-    x[p] = v1;
-    x[h + p] = v2;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int j = a.j;
-    a.T[(int64_t)(j + 1) * a.ldt + j] = beta;
-    if (j + 1 < a.m) a.T[(int64_t)j * a.ldt + j + 1] = beta;
-    if (brk) st->status = 5;
-  }
-}
-
-// ------------------------------------------------------------------ one cooperative launch per step
-// The compensated-FP32 Gram-Schmidt of one Lanczos step (alpha, every pass with the sqrt(2) test,
-// normalisation) as one cooperative launch, like gs_step_coop_kernel in gs.cu: grid-wide barriers
-// where the multi-kernel path ends one launch and starts the next; each block walks row blocks
-// rb = blockIdx.x, blockIdx.x + gridDim.x, ... of the same partition; every block takes the test from
-// the same partials in the same order; nrm2 holds two slots of nblk norm partials.
-__device__ double dfupdate_rows(const GSArgs& a, int64_t p0, int64_t p1, const float4* scf, float (*red_s)[32][4],
-                                float (*red_e)[32][4]) {
+// y -= V c_v + W c_w with every 32-row chunk shared by all warps: warp q takes columns q, q + 8, ...,
+// the eight compensated partial sums are added (still compensated) by warp 0, which updates y in FP64.
+__device__ double dfupdate_split(const GSArgs& a, int64_t p0, int64_t p1, const float4* scf, float (*red_s)[32][4],
+                                 float (*red_e)[32][4]) {
   const float4* V = (const float4*)a.V;
   double2* y = (double2*)a.y;
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
@@ -399,6 +385,72 @@ __device__ double dfupdate_rows(const GSArgs& a, int64_t p0, int64_t p1, const f
   }
   return nrm;
 }
+
+__global__ void __launch_bounds__(kThreads) gsdf_update_kernel(GSArgs a) {
+  extern __shared__ float4 scf[];                       // per column: {cv hi/lo}, {cw hi/lo}
+  __shared__ double sh[32];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = a.st->done;
+  __syncthreads();
+  if (s_skip) return;
+  const int j = a.j;
+  for (int i = threadIdx.x; i <= j; i += kThreads) {
+    const coef4 c = a.coef[i];
+    scf[2 * i] = split(make_double2(c.vr, c.vi));
+    scf[2 * i + 1] = split(make_double2(c.wr, c.wi));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.st->units_update += (double)(j + 1) * (double)a.h;
+  __syncthreads();
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, a.h);
+  __shared__ float red_s[kGroups][32][4], red_e[kGroups][32][4];
+  const double nrm = block_sum(dfupdate_rows(a, p0, p1, scf, red_s, red_e), sh);
+  if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
+}
+
+// v_{j+1} = y / beta stored split into V4[:, j+1] and in FP64 into x (the next matvec input).
+__global__ void __launch_bounds__(kThreads) gsdf_normalize_kernel(GSArgs a, double2* __restrict__ x) {
+  __shared__ double sh[32];
+  StepState* st = a.st;
+  const int done = st->done;
+  double beta;
+  if (done) {
+    beta = st->beta;
+  } else {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < a.nblk; b += kThreads) s += a.part_nrm[b];
+    beta = sqrt(block_sum(s, sh));
+  }
+  const double tmax = st->tmax;
+  const bool brk = !(beta > 1e-14 * fmax(tmax, 1.0));
+  const double inv = brk ? 0.0 : 1.0 / beta;
+  const double2* y = (const double2*)a.y;
+  float4* v = (float4*)a.V + (int64_t)(a.j + 1) * a.n;
+  const int64_t h = a.h;
+  const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
+  const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
+    const double2 y1 = y[p], y2 = y[h + p];
+    const double2 v1 = make_double2(y1.x * inv, y1.y * inv), v2 = make_double2(y2.x * inv, y2.y * inv);
+    v[p] = split(v1);
+    v[h + p] = split(v2);
+    x[p] = v1;
+    x[h + p] = v2;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int j = a.j;
+    a.T[(int64_t)(j + 1) * a.ldt + j] = beta;
+    if (j + 1 < a.m) a.T[(int64_t)j * a.ldt + j + 1] = beta;
+    if (brk) st->status = 5;
+  }
+}
+
+// ------------------------------------------------------------------ one cooperative launch per step
+// The compensated-FP32 Gram-Schmidt of one Lanczos step (alpha, every pass with the sqrt(2) test,
+// normalisation) as one cooperative launch, like gs_step_coop_kernel in gs.cu: grid-wide barriers
+// where the multi-kernel path ends one launch and starts the next; each block walks row blocks
+// rb = blockIdx.x, blockIdx.x + gridDim.x, ... of the same partition; every block takes the test from
+// the same partials in the same order; nrm2 holds two slots of nblk norm partials.
 
 __device__ __forceinline__ double coop_norm_df(const double* part, int nblk, double* sh) {
   double s = 0.0;
