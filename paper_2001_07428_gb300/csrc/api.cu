@@ -332,12 +332,18 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
     if (op->kind == JTRLAN_STENCIL4D) {   // (hi, lo) links for the compensated-FP32 matvec
       OpDev& d = c->pdf.opdf;
       d = o;
-      float4 *u = nullptr, *w = nullptr;
-      JT_TRY(c->dalloc(&u, (size_t)36 * o.vol * sizeof(float4)));
-      JT_TRY(c->dalloc(&w, (size_t)36 * o.vol * sizeof(float4)));
-      JT_CUDA(launch_links_df(o.U, u, o.vol, c->stream));
-      JT_CUDA(launch_links_df(o.W, w, o.vol, c->stream));
-      d.U = u; d.W = w;
+      if (op->dtype == JTRLAN_C64) {
+        // the caller's links are complex64, so they are exact in FP32: the compensated kernels read
+        // the FP32 phase's structure-of-arrays copy (set below) as (hi, 0) pairs
+        d.links32 = 1;
+      } else {
+        float4 *u = nullptr, *w = nullptr;
+        JT_TRY(c->dalloc(&u, (size_t)36 * o.vol * sizeof(float4)));
+        JT_TRY(c->dalloc(&w, (size_t)36 * o.vol * sizeof(float4)));
+        JT_CUDA(launch_links_df(o.U, u, o.vol, c->stream));
+        JT_CUDA(launch_links_df(o.W, w, o.vol, c->stream));
+        d.U = u; d.W = w;
+      }
       c->pdf.dfmv = true;
       const int nb = matvec_df_blocks(d);
       if (nb > c->pdf.mv_nblk) JT_TRY(c->dalloc(&c->pdf.alpha_part, (size_t)nb * sizeof(double2)));
@@ -363,6 +369,10 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
       JT_CUDA(launch_links_soa(o.U, u, o.vol, c->stream));
       JT_CUDA(launch_links_soa(o.W, w, o.vol, c->stream));
       q.U = u; q.W = w;
+      if (c->pdf.opdf.links32) {
+        c->pdf.opdf.U = u;
+        c->pdf.opdf.W = w;
+      }
     } else {
       float2 *a = nullptr, *b = nullptr;
       JT_TRY(c->dalloc(&a, (size_t)c->h * c->h * sizeof(float2)));

@@ -728,12 +728,18 @@ struct DfSums {
   float ys1[2], ye1[2], ys2[2], ye2[2], ws1[2], we1[2], ws2[2], we2[2];
 };
 
+// A link as a (hi, lo) pair: either stored so, or exact in FP32 (lo = 0, which the compiler folds
+// out of every product).
+__device__ __forceinline__ float4 link4(float4 l) { return l; }
+__device__ __forceinline__ float4 link4(float2 l) { return make_float4(l.x, l.y, 0.f, 0.f); }
+
+template <typename LinkT>
 __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* __restrict__ x, int s, int a,
                                                 DfSums& r) {
   const int vol = (int)op.vol;
   const int64_t h = op.h;
-  const float4* U = (const float4*)op.U;
-  const float4* W = (const float4*)op.W;
+  const LinkT* U = (const LinkT*)op.U;
+  const LinkT* W = (const LinkT*)op.W;
   const float4* x1 = x;
   const float4* x2 = x + h;
 #pragma unroll
@@ -753,16 +759,16 @@ __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* _
     const int sp = (c == L - 1) ? s - (L - 1) * stride : s + stride;
     const int sm = (c == 0) ? s + (L - 1) * stride : s - stride;
     stride *= L;
-    const float4* Um = U + (int64_t)mu * 9 * vol;
-    const float4* Wm = W + (int64_t)mu * 9 * vol;
+    const LinkT* Um = U + (int64_t)mu * 9 * vol;
+    const LinkT* Wm = W + (int64_t)mu * 9 * vol;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const float4 p1 = x1[3 * sp + b], p2 = x2[3 * sp + b];
       const float4 m1 = x1[3 * sm + b], m2 = x2[3 * sm + b];
-      const float4 uf = Um[(a * 3 + b) * vol + s];    // U(s)_{ab}
-      const float4 ub = Um[(b * 3 + a) * vol + sm];   // U(s-mu)_{ba}
-      const float4 wf = Wm[(a * 3 + b) * vol + s];    // W(s)_{ab}
-      const float4 wb = Wm[(b * 3 + a) * vol + sm];   // W(s-mu)_{ba}
+      const float4 uf = link4(Um[(a * 3 + b) * vol + s]);    // U(s)_{ab}
+      const float4 ub = link4(Um[(b * 3 + a) * vol + sm]);   // U(s-mu)_{ba}
+      const float4 wf = link4(Wm[(a * 3 + b) * vol + s]);    // W(s)_{ab}
+      const float4 wb = link4(Wm[(b * 3 + a) * vol + sm]);   // W(s-mu)_{ba}
       cdf_acc(r.ys1, r.ye1, uf, p1);           // U(s) x1(s+mu)
       cdf_accc(r.ys1, r.ye1, ub, m1);          // U(s-mu)^H x1(s-mu)
       cdf_accc(r.ys2, r.ye2, uf, p2);          // U(s)^* x2(s+mu)
@@ -775,6 +781,7 @@ __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* _
   }
 }
 
+template <typename LinkT>
 __global__ void __launch_bounds__(3 * kDfSites, kDfMinBlocks)
 stencil_df_kernel(OpDev op, const float4* __restrict__ x, double2* __restrict__ Y, double* __restrict__ part) {
   __shared__ double sh[32];
@@ -785,7 +792,7 @@ stencil_df_kernel(OpDev op, const float4* __restrict__ x, double2* __restrict__ 
   double c0 = 0.0, c1 = 0.0;
   if (s < vol) {
     DfSums r;
-    stencil_df_sums(op, x, s, a, r);
+    stencil_df_sums<LinkT>(op, x, s, a, r);
     const int64_t e1 = 3 * (int64_t)s + a;
     const double2 xa = join(x[e1]), xb = join(x[h + e1]);
     const double kap = op.kappa, m0 = op.m0;
@@ -849,6 +856,7 @@ struct ChebConsts {
 // t_next feeds the next product directly.  On the last step acc goes out in FP64 to y, with the
 // per-block partials of conj(v) y (the alpha of Algorithm 2).  t_next may alias t_prev (the same
 // thread reads an entry before writing it); neighbours are read from x only.
+template <typename LinkT>
 __global__ void __launch_bounds__(3 * kDfSites, kDfMinBlocks)
 stencil_df_cheb_kernel(OpDev op, const float4* __restrict__ x, const float4* t_prev, float4* t_next,
                        float4* __restrict__ acc, const float4* __restrict__ v, double2* __restrict__ y,
@@ -861,7 +869,7 @@ stencil_df_cheb_kernel(OpDev op, const float4* __restrict__ x, const float4* t_p
   double c0 = 0.0, c1 = 0.0;
   if (s < vol) {
     DfSums r;
-    stencil_df_sums(op, x, s, a, r);
+    stencil_df_sums<LinkT>(op, x, s, a, r);
     const int64_t e1 = 3 * (int64_t)s + a;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -1008,7 +1016,10 @@ cudaError_t launch_gather_pairs_df(const void* V, int64_t n, const int* order, i
 int matvec_df_blocks(const OpDev& op) { return (int)((op.vol + kDfSites - 1) / kDfSites); }
 
 cudaError_t launch_matvec_df(const OpDev& op, const void* x, void* y, double* part, cudaStream_t s) {
-  stencil_df_kernel<<<matvec_df_blocks(op), 3 * kDfSites, 0, s>>>(op, (const float4*)x, (double2*)y, part);
+  if (op.links32)
+    stencil_df_kernel<float2><<<matvec_df_blocks(op), 3 * kDfSites, 0, s>>>(op, (const float4*)x, (double2*)y, part);
+  else
+    stencil_df_kernel<float4><<<matvec_df_blocks(op), 3 * kDfSites, 0, s>>>(op, (const float4*)x, (double2*)y, part);
   return cudaGetLastError();
 }
 
@@ -1017,9 +1028,14 @@ cudaError_t launch_matvec_df_cheb(const OpDev& op, const void* x, const void* t_
                                   double g, double g0, int init, int last, cudaStream_t s) {
   auto f = [](double d) { const float hi = (float)d; return ff{hi, (float)(d - (double)hi)}; };
   ChebConsts k{f(kappa), f(m0), f(c), f(sc), f(g), f(g0)};
-  stencil_df_cheb_kernel<<<matvec_df_blocks(op), 3 * kDfSites, 0, s>>>(
-      op, (const float4*)x, (const float4*)t_prev, (float4*)t_next, (float4*)acc, (const float4*)v, (double2*)y,
-      part, k, init, last);
+  if (op.links32)
+    stencil_df_cheb_kernel<float2><<<matvec_df_blocks(op), 3 * kDfSites, 0, s>>>(
+        op, (const float4*)x, (const float4*)t_prev, (float4*)t_next, (float4*)acc, (const float4*)v, (double2*)y,
+        part, k, init, last);
+  else
+    stencil_df_cheb_kernel<float4><<<matvec_df_blocks(op), 3 * kDfSites, 0, s>>>(
+        op, (const float4*)x, (const float4*)t_prev, (float4*)t_next, (float4*)acc, (const float4*)v, (double2*)y,
+        part, k, init, last);
   return cudaGetLastError();
 }
 

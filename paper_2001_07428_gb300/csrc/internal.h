@@ -22,6 +22,8 @@ struct OpDev {
   const void* U;       // stencil links: FP64 [4][V][9]; FP32 structure-of-arrays [4][9][V]
   const void* W;
   int fp32;            // 1: FP32 operator (float2 links / blocks), 0: FP64
+  int links32;         // compensated-FP32 stencil: 1 = links exact in FP32 (float2 SoA, the caller's
+                       // complex64 links), 0 = (hi, lo) float4 SoA
 };
 
 // Modes of the matvec kernels.

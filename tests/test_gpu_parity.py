@@ -248,3 +248,25 @@ def test_mixed_stencil_8x8x8x8_matches_golden(precision):
     assert (stats["n_matvec_fp32"] > 0) == (precision == "mixed")
     _check_pairs(ev, X, mv, 1e-8, np.array(g["evals"]))
     assert np.all(res < 1e-8)
+
+
+def test_mixed_reorth_complex64_links_match_brute_force():
+    """Complex64 links are exact in FP32: the compensated products read them as (hi, 0) pairs.  The
+    eigenvalues must match brute-force diagonalisation of the operator those links define."""
+    dims = (4, 4, 4, 4)
+    U, W = inputs.stencil_links(dims, 5)
+    U32 = U.astype(np.complex64).astype(np.complex128)
+    W32 = W.astype(np.complex64).astype(np.complex128)
+    n = 6 * inputs.lattice_volume(dims)
+    mv = lambda x: jsym.stencil_matvec(U32, W32, dims, 8.5, 0.3, x)
+    A = np.stack([mv(e) for e in np.eye(n, dtype=np.complex128)], axis=1)
+    bf = np.linalg.eigvalsh(A)[0::2][:8]
+    s = _solver(kind="stencil", dims=dims, m0=8.5, kappa=0.3, U=U.astype(np.complex64), W=W.astype(np.complex64),
+                nev=8, m=30, mwin=15, tol=1e-10, precision="mixed_reorth", links_dtype="c64")
+    s.solve()
+    ev, X, res = s.pairs()
+    s.close()
+    assert np.abs(ev - bf).max() < 1e-10 * np.abs(bf).max()
+    Xh = X.cpu().numpy()
+    for i in range(8):
+        assert np.linalg.norm(mv(Xh[:, i]) - ev[i] * Xh[:, i]) < 1e-10
