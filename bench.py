@@ -158,9 +158,11 @@ def cpu_baseline(name, full_products, restarts=4):
 
 
 # ---------------------------------------------------------------- the mixed form where it is quoted
-def mixed_at_16(B, torch, stream, flush):
+def mixed_at_16(B, torch, stream, flush, profiled_ms=None):
     """One timed solve each of plain FP64 and the double-float mixed form on the 16^4 workload
-    (n = 393,216, nev = 50, m = 120, mwin = 60), after one untimed warm-up solve of each."""
+    (n = 393,216, nev = 50, m = 120, mwin = 60), after one untimed warm-up solve of each; with
+    `profiled_ms` (a function of a context returning per-kernel device times) also one profiled
+    solve of each."""
     import ctypes
     w = inputs.WORKLOADS["stencil_16x16x16x16"]
     dims = w["dims"]
@@ -187,6 +189,11 @@ def mixed_at_16(B, torch, stream, flush):
         evs[name] = ev
         out[name] = {"value": e0.elapsed_time(e1) / 1e3, "unit": "s", "n_matvec": st["n_matvec"],
                      "n_restarts": st["n_restarts"], "max_residual": float(res.max())}
+        if profiled_ms is not None:
+            ctxp = B.jtrlan_create(op, B.params(w["nev"], w["m"], w["mwin"], TOL, precision=prec, profile=1),
+                                   stream.cuda_stream)
+            out[name]["kernels"] = profiled_ms(ctxp)
+            B.jtrlan_destroy(ctxp)
     out["speedup_vs_fp64"] = round(out["fp64"]["value"] / out["mixed_reorth"]["value"], 3)
     out["max_rel_eig_diff_vs_fp64"] = float(np.max(np.abs(evs["mixed_reorth"] - evs["fp64"]) / np.abs(evs["fp64"])))
     return out
@@ -696,14 +703,13 @@ def run_gb300(args, rank, world, local_rank):
     invert = invert_compare(B, torch, stream, flush, op, w, t_mean, ev64)
 
     # ---- one profiled solve per form: per-kernel device time
-    def profiled(precision):
-        ctxp = B.jtrlan_create(op, B.params(w["nev"], w["m"], w["mwin"], TOL, precision=precision, profile=1),
-                               stream.cuda_stream)
+    def profiled_ctx(ctxp):
+        """one solve of a context created with profile=1: per-kernel-class device time, launches,
+        share and (where the work per unit is defined) achieved TFLOP/s and GB/s"""
         flush.zero_()
         torch.cuda.synchronize()
         B.jtrlan_solve(ctxp)
         prof = B.jtrlan_get_profile(ctxp)
-        B.jtrlan_destroy(ctxp)
         tot_ms = sum(v["ms"] for v in prof.values())
         out = {}
         for k, v in prof.items():
@@ -717,10 +723,17 @@ def run_gb300(args, rank, world, local_rank):
             out[k] = e
         return out
 
+    def profiled(precision):
+        ctxp = B.jtrlan_create(op, B.params(w["nev"], w["m"], w["mwin"], TOL, precision=precision, profile=1),
+                               stream.cuda_stream)
+        out = profiled_ctx(ctxp)
+        B.jtrlan_destroy(ctxp)
+        return out
+
     kernels = profiled(B.JTRLAN_FP64)
     mixed["kernels_" + mixed["chosen"]] = profiled(forms[mixed["chosen"]][0])
     if not args.no_mixed_16:
-        mixed["stencil_16x16x16x16"] = mixed_at_16(B, torch, stream, flush)
+        mixed["stencil_16x16x16x16"] = mixed_at_16(B, torch, stream, flush, profiled_ctx)
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     hbm_peak, hbm_src = measured_peaks()
     if "tflops" in kernels[dom]:
