@@ -4,7 +4,7 @@ Written from Sec. 3 of Ishikawa & Sogabe in the paper's order and notation.  Ind
 are 0-based here: column j of V is the paper's v_{j+1}.  W = J V* is formed column by
 column where Algorithm 2 uses it, exactly as the paper states it.
 
-Readings where the paper is silent or ambiguous (each also listed in the design doc):
+Readings where the paper is silent or ambiguous:
 
 R1  Algorithm 2 divides by b0 after its Gram-Schmidt loop; on exit b0 still holds the
     norm before the last pass.  We normalise by the norm after the last pass (b1)

@@ -108,8 +108,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
-                           "(python -m paper_2001_07428_gb300.build)")
+        raise RuntimeError(f"{path} is missing: build it with python -m paper_2001_07428_gb300.build")
     lib = ctypes.CDLL(path)
     P = ctypes.POINTER
     lib.jtrlan_create.argtypes = [P(jtrlan_operator), P(jtrlan_params), ctypes.c_void_p,

@@ -353,7 +353,7 @@ rotate_tc_kernel(const float4* __restrict__ V, int64_t n, int m, int nkc, int ns
     int it = 0;
     for (int64_t mt = grp; mt < mtiles; mt += ngrp, ++it) {
       const int buf = it & 1;
-      // tcgen05.ld is warp-collective: one lane waits and the whole warp takes its verdict
+      // tcgen05.ld is warp-collective: one lane waits and the whole warp takes its result
       bool ok = true;
       if (lane == 0) ok = mbar_wait(saddr(&bars->accfull[buf]), (uint32_t)((it >> 1) & 1), bars, err, 5);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
