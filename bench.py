@@ -74,6 +74,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# ---------------------------------------------------------------- ranks (replicas: no collective on the data path)
+def max_over_ranks(value, world, device):
+    """The largest `value` over the ranks: every rank runs the same solve on its own GPU, and the job
+    is as slow as its slowest replica.  `device` holds the collective's tensor (cuda under NCCL, cpu
+    under gloo)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- clocks during the timed region
 class Clocks:
     FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
@@ -663,11 +677,7 @@ def run_gb300(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
     times = [a.elapsed_time(b) / 1e3 for a, b in zip(ev0, ev1)]
-    t_mean = statistics.mean(times)
-    if world > 1:
-        t = torch.tensor([t_mean], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_mean = float(t.item())
+    t_mean = max_over_ranks(statistics.mean(times), world, dev)
 
     # ---- the chosen (mixed-precision) form on the same workload: time and agreement with FP64
     ev64 = np.zeros(w["nev"])
@@ -770,11 +780,7 @@ def run_gb300(args, rank, world, local_rank):
                        resh.ctypes.data_as(ctypes.c_void_p))
         B.jtrlan_destroy(c2)
         e2e.append(time.perf_counter() - t0)
-    e2e_mean = statistics.mean(e2e)
-    if world > 1:
-        t = torch.tensor([e2e_mean], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_mean = float(t.item())
+    e2e_mean = max_over_ranks(statistics.mean(e2e), world, dev)
     h2d = Uh.numel() * 16 + Wh.numel() * 16
     d2h = Xh.numel() * 16 + 2 * w["nev"] * 8
     B.jtrlan_destroy(ctx)
