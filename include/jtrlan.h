@@ -280,13 +280,16 @@ jtrlan_status jtrlan_residual_norms_noalloc(const jtrlan_operator* op, const voi
  *   Z: device, m x kk FP64, column-major (column c at Z + c m); |Z| < 2^120.
  *   out: device, n x kk complex128, column-major, written; must not overlap V or Z.
  *   path: 0 = tensor cores (tcgen05, BF16 digit splitting with exact FP32 accumulation; needs
- *     m <= 320), 1 = compensated FP32 on the CUDA cores (any m).
+ *     m <= 320), 1 = compensated FP32 on the CUDA cores (any m), 2 = a self-test of the tensor-core
+ *     kernel's failure path: one accumulator barrier is never signalled, the kernel's bounded wait
+ *     (about 2 s) runs out, the kernel frees its tensor memory and returns, and the call returns
+ *     JTRLAN_ETIMEOUT with out undefined; the stream stays usable.
  * Each entry agrees with the exact product of the given values to about 2^-49 m max_k |V_rk|
  * max_k |Z_kc| on either path (on path 0 a row of the real view whose entries all lie below 2^-120
  * is resolved to 2^-169 absolute instead; path 1 multiplies FP32 pairs, so there the bound needs
  * every nonzero product |V_rk Z_kc| above 2^-100 and every |Z| below 2^100).  The call allocates and frees its scratch (row and column exponents,
  * the BF16 digits of Z) and synchronises the stream.
- * Errors: JTRLAN_EINVAL (null pointers, n < 1, m < 1, kk < 1, path 0 with m > 320, path not 0/1),
+ * Errors: JTRLAN_EINVAL (null pointers, n < 1, m < 1, kk < 1, path 0 or 2 with m > 320, path not 0/1/2),
  * JTRLAN_ENOMEM, JTRLAN_ECUDA, JTRLAN_ETIMEOUT (a bounded wait inside the tensor-core kernel ran
  * out; the stream stays usable). */
 jtrlan_status jtrlan_rotate_df(const void* V, int64_t n, int m, const double* Z, int kk, void* out, int path,

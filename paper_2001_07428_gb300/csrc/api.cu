@@ -1176,8 +1176,8 @@ jtrlan_status jtrlan_rotate_df(const void* V, int64_t n, int m, const double* Z,
                                void* cuda_stream) {
   if (!V || !Z || !out) return fail(JTRLAN_EINVAL, "null argument");
   if (n < 1 || m < 1 || kk < 1) return fail(JTRLAN_EINVAL, "need n, m, kk >= 1");
-  if (path != 0 && path != 1) return fail(JTRLAN_EINVAL, "path must be 0 (tensor cores) or 1 (CUDA cores)");
-  if (path == 0 && m > tc_rotate_max_m())
+  if (path < 0 || path > 2) return fail(JTRLAN_EINVAL, "path must be 0 (tensor cores), 1 (CUDA cores) or 2 (self-test)");
+  if (path != 1 && m > tc_rotate_max_m())
     return fail(JTRLAN_EINVAL, "tensor-core rotation needs m <= " + std::to_string(tc_rotate_max_m()));
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (path == 1) {
@@ -1191,7 +1191,7 @@ jtrlan_status jtrlan_rotate_df(const void* V, int64_t n, int m, const double* Z,
   TcWork w = tc_rotate_carve(base, n, m, kk);
   int herr = 0;
   e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = launch_rotate_tc(V, n, m, Z, kk, out, w, true, s);
+  if (e == cudaSuccess) e = launch_rotate_tc(V, n, m, Z, kk, out, w, true, s, path == 2 ? 1 : 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(base);

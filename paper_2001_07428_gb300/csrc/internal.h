@@ -117,8 +117,10 @@ int tc_rotate_max_m();
 size_t tc_rotate_bytes(int64_t n, int m, int kk_max);
 TcWork tc_rotate_carve(void* base, int64_t n, int m, int kk_max);
 // fresh_rowexp: recompute the row exponents of V (false: V is unchanged since the last call)
+// selftest = 1: the first tile's accumulator barrier is never signalled, so a bounded wait runs out and
+// w.err is set (the failure path, without a fault; the output is then undefined).
 cudaError_t launch_rotate_tc(const void* V, int64_t n, int m, const double* Z, int kk, void* out, const TcWork& w,
-                             bool fresh_rowexp, cudaStream_t s);
+                             bool fresh_rowexp, cudaStream_t s, int selftest = 0);
 // Stencil y (FP64) = A x with x and the links as (hi, lo) pairs; part (may be null) receives the
 // block partials of x^H y.  op.U / op.W: (hi, lo) links, structure-of-arrays [4][9][V].
 int matvec_df_blocks(const OpDev& op);

@@ -213,7 +213,7 @@ __device__ __forceinline__ double tc_combine(float h, float l, int es) {
 __global__ void __launch_bounds__(kThreads, 1)
 rotate_tc_kernel(const float4* __restrict__ V, int64_t n, int m, int nkc, int nst, const int8_t* __restrict__ Erow,
                  const uint8_t* __restrict__ Bimg, const int* __restrict__ Ecol, int kk, int ntn, int ngrp,
-                 int64_t mtiles, double* __restrict__ out, int* err) {
+                 int64_t mtiles, double* __restrict__ out, int* err, int selftest) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* Bs = sm;                                  // nkc chunks x 7 planes x 1 KB
@@ -282,7 +282,9 @@ rotate_tc_kernel(const float4* __restrict__ V, int64_t n, int m, int nkc, int ns
           umma_commit(saddr(&bars->empty[st]));
         }
         if (!ok) break;
-        umma_commit(saddr(&bars->accfull[buf]));
+        // selftest: the first tile's accumulator barrier is never signalled, so the epilogue's bounded
+        // wait runs out (the failure path, exercised without a fault)
+        if (!(selftest && it == 0)) umma_commit(saddr(&bars->accfull[buf]));
       }
     }
     __syncwarp();
@@ -481,7 +483,7 @@ TcWork tc_rotate_carve(void* base, int64_t n, int m, int kk_max) {
 }
 
 cudaError_t launch_rotate_tc(const void* V, int64_t n, int m, const double* Z, int kk, void* out, const TcWork& w,
-                             bool fresh_rowexp, cudaStream_t s) {
+                             bool fresh_rowexp, cudaStream_t s, int selftest) {
   if (m < 1 || m > tc_rotate_max_m() || kk < 1 || kk > w.kk_max || n != w.n || m != w.m) return cudaErrorInvalidValue;
   if (g_nsm == 0) {
     int dev = 0;
@@ -511,7 +513,7 @@ cudaError_t launch_rotate_tc(const void* V, int64_t n, int m, const double* Z, i
   }
   const int ngrp = (int)std::min<int64_t>(std::max(1, g_nsm / ntn), mtiles);
   rotate_tc_kernel<<<ntn * ngrp, kThreads, smem, s>>>((const float4*)V, n, m, nkc, nst, w.Erow, w.Bimg, w.Ecol, kk,
-                                                       ntn, ngrp, mtiles, (double*)out, w.err);
+                                                       ntn, ngrp, mtiles, (double*)out, w.err, selftest);
   return cudaGetLastError();
 }
 

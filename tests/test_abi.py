@@ -186,7 +186,8 @@ def test_rotate_df_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.jtrlan_rotate_df(d, 0, 4, d, 2, d, 0, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_rotate_df(d, 10, 0, d, 2, d, 0, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_rotate_df(d, 10, 4, d, 0, d, 0, None) == B.JTRLAN_EINVAL
-    assert lib.jtrlan_rotate_df(d, 10, 4, d, 2, d, 2, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_rotate_df(d, 10, 4, d, 2, d, 3, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_rotate_df(d, 10, 321, d, 2, d, 2, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_rotate_df(d, 10, 321, d, 2, d, 0, None) == B.JTRLAN_EINVAL   # tensor cores: m <= 320
     assert "320" in lib.jtrlan_last_error().decode()
 

@@ -162,3 +162,22 @@ def test_solver_rotation_paths_agree():
     mv = lambda x: jsym.stencil_matvec(U, W, dims, 8.5, 0.3, x)
     for i in range(0, 20, 5):
         assert np.linalg.norm(mv(X0[:, i]) - e0[i] * X0[:, i]) < 1e-8
+
+
+def test_bounded_wait_reports_timeout_and_the_stream_stays_usable():
+    """path 2 leaves one accumulator barrier unsignalled: the kernel's bounded wait (about 2 s) runs
+    out, it frees its tensor memory and returns, and the call reports JTRLAN_ETIMEOUT; the next call
+    on the same stream computes the right product."""
+    import time
+    from paper_2001_07428_gb300 import binding as B
+    rng = np.random.default_rng(21)
+    n, m, kk = 4096, 32, 32
+    Vc = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(2 * n)
+    Z = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    Vd, Vx = _pack(Vc)
+    t0 = time.perf_counter()
+    with pytest.raises(B.JTRLanError) as ei:
+        _rotate(Vd, n, m, Z, 2)
+    assert ei.value.status == B.JTRLAN_ETIMEOUT
+    assert 0.5 < time.perf_counter() - t0 < 60.0
+    _check(_rotate(Vd, n, m, Z, 0), Vx, Z)
