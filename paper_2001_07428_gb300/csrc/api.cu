@@ -160,6 +160,8 @@ struct jtrlan_ctx {
   CgState* cg_st = nullptr;
   CgState* h_cgst = nullptr;       // pinned copy
   int64_t cg_matvecs = 0, cg_iters = 0;
+  cudaGraphExec_t cg_group = nullptr;   // kCgGroup CG iterations captured once (buffers are the context's)
+  const void* cg_group_y = nullptr;     // the solution buffer the graph writes
   TcWork tc{};                     // scratch of the tensor-core rotation (compensated-FP32 basis)
   bool tc_on = false;
   int* h_tcerr = nullptr;          // pinned copy of its error flag
@@ -195,6 +197,7 @@ struct jtrlan_ctx {
   }
   ~jtrlan_ctx() {
     cudaStreamSynchronize(stream);
+    if (cg_group) cudaGraphExecDestroy(cg_group);
     for (void* p : owned) cudaFree(p);
     for (void* p : owned_host) cudaFreeHost(p);
   }
@@ -627,13 +630,53 @@ jtrlan_status cg_solve(jtrlan_ctx* c, Phase& ph, const void* b, void* y) {
   const int max_iter = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : 10000;
   LAUNCH(K_CG, launch_cg_init(b, y, c->cg_r, c->cg_p, n, c->cg_part, rtol, c->cg_st, s));
   c->nl[K_CG] += 1;   // two kernels
-  for (int launched = 0;;) {
+  auto group = [&](cudaStream_t st) -> cudaError_t {
     for (int u = 0; u < kCgGroup; ++u) {
-      LAUNCH(K_CG, launch_matvec<double>(ph.op, (const double2*)c->cg_p, (double2*)c->cg_q, MV_ALPHA, c->cg_pq,
-                                         nullptr, nullptr, 0, 0, nullptr, s));
-      LAUNCH(K_CG, launch_cg_alpha(c->cg_pq, ph.mv_nblk, c->cg_st, s));
-      LAUNCH(K_CG, launch_cg_update(y, c->cg_r, c->cg_p, c->cg_q, n, c->cg_part, c->cg_st, s));
-      c->nl[K_CG] += 2;   // three kernels
+      cudaError_t e = launch_matvec<double>(ph.op, (const double2*)c->cg_p, (double2*)c->cg_q, MV_ALPHA, c->cg_pq,
+                                            nullptr, nullptr, 0, 0, nullptr, st);
+      if (e == cudaSuccess) e = launch_cg_alpha(c->cg_pq, ph.mv_nblk, c->cg_st, st);
+      if (e == cudaSuccess) e = launch_cg_update(y, c->cg_r, c->cg_p, c->cg_q, n, c->cg_part, c->cg_st, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (!c->prof.on && (!c->cg_group || c->cg_group_y != y)) {
+    // capture the group once, on a private stream (the caller's may be the legacy default stream,
+    // which cannot be captured); the graph then replays on the context stream
+    if (c->cg_group) {
+      cudaGraphExecDestroy(c->cg_group);
+      c->cg_group = nullptr;
+    }
+    cudaStream_t cap = nullptr;
+    JT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e1 = group(cap);
+      e = cudaStreamEndCapture(cap, &gr);
+      if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->cg_group, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+      c->cg_group = nullptr;
+      return fail(JTRLAN_ECUDA, std::string("CG graph: ") + cudaGetErrorString(e));
+    }
+    c->cg_group_y = y;
+  }
+  for (int launched = 0;;) {
+    if (c->prof.on) {   // the per-kernel profile needs every launch bracketed by events
+      for (int u = 0; u < kCgGroup; ++u) {
+        LAUNCH(K_CG, launch_matvec<double>(ph.op, (const double2*)c->cg_p, (double2*)c->cg_q, MV_ALPHA, c->cg_pq,
+                                           nullptr, nullptr, 0, 0, nullptr, s));
+        LAUNCH(K_CG, launch_cg_alpha(c->cg_pq, ph.mv_nblk, c->cg_st, s));
+        LAUNCH(K_CG, launch_cg_update(y, c->cg_r, c->cg_p, c->cg_q, n, c->cg_part, c->cg_st, s));
+        c->nl[K_CG] += 2;   // three kernels
+      }
+    } else {
+      JT_CUDA(cudaGraphLaunch(c->cg_group, s));
+      c->nl[K_CG] += 5 * kCgGroup;
     }
     launched += kCgGroup;
     c->cg_matvecs += kCgGroup;
