@@ -11,7 +11,8 @@
 // with one exponent E per row of V (|x| < 2^E along the row) and one, F, per column of Z.  A digit
 // has at most 8 significant bits, so it is exact in BF16 and a digit product is exact in FP32.
 // For the d-th accumulator P_d = sum_k sum_{s+t=d} a_s b_t every partial sum is an integer of
-// magnitude below m * 9 * 2^12 < 2^24 (m <= 455), so the tensor core adds without rounding.  The 28
+// magnitude below m * 9 * 2^12 < 2^24 (m <= 455; shared memory limits this kernel to m <= 320), so the
+// tensor core adds without rounding.  The 28
 // digit pairs with s + t <= 6 feed 7 accumulators (one per d); the epilogue forms
 // sum_d 2^(-7d) P_d in float-float and scales it by 2^(E + F - 14).  Each dropped pair (s + t >= 7)
 // and each digit remainder is below 2^-49 of max_k |V_rk| max_k |Z_kc| per product, the accuracy of
@@ -456,8 +457,6 @@ __global__ void tc_zslice_kernel(const double* __restrict__ Z, int m, int kk, in
   }
 }
 
-int g_nsm = 0;
-
 }  // namespace
 
 int tc_rotate_max_m() { return 320; }
@@ -485,16 +484,14 @@ TcWork tc_rotate_carve(void* base, int64_t n, int m, int kk_max) {
 cudaError_t launch_rotate_tc(const void* V, int64_t n, int m, const double* Z, int kk, void* out, const TcWork& w,
                              bool fresh_rowexp, cudaStream_t s, int selftest) {
   if (m < 1 || m > tc_rotate_max_m() || kk < 1 || kk > w.kk_max || n != w.n || m != w.m) return cudaErrorInvalidValue;
-  if (g_nsm == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
+  int dev = 0, nsm = 0;   // per device: queried on every call (cheap), as is the attribute below
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e0 != cudaSuccess) return e0;
   const int nkc = (m + kTcK - 1) / kTcK, ntn = (kk + kTcCols - 1) / kTcCols;
   const int64_t mtiles = (2 * n + kTcRows - 1) / kTcRows;
   if (fresh_rowexp) {
-    const int64_t nb = std::min<int64_t>((n + 255) / 256, (int64_t)g_nsm * 8);
+    const int64_t nb = std::min<int64_t>((n + 255) / 256, (int64_t)nsm * 8);
     tc_rowexp_kernel<<<(unsigned)nb, 256, 0, s>>>((const float4*)V, n, m, w.Erow);
   }
   tc_zslice_kernel<<<ntn * kTcCols, 128, 0, s>>>(Z, m, kk, nkc, (uint16_t*)w.Bimg, w.Ecol);
@@ -505,13 +502,11 @@ cudaError_t launch_rotate_tc(const void* V, int64_t n, int m, const double* Z, i
   if (nst < 2) return cudaErrorInvalidValue;
   size_t smem = fixed + (size_t)nst * kStageA;
   if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: each holds all 512 tensor-memory columns
-  static bool attr = false;
-  if (!attr) {
+  {
     cudaError_t e = cudaFuncSetAttribute(rotate_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
-  const int ngrp = (int)std::min<int64_t>(std::max(1, g_nsm / ntn), mtiles);
+  const int ngrp = (int)std::min<int64_t>(std::max(1, nsm / ntn), mtiles);
   rotate_tc_kernel<<<ntn * ngrp, kThreads, smem, s>>>((const float4*)V, n, m, nkc, nst, w.Erow, w.Bimg, w.Ecol, kk,
                                                        ntn, ngrp, mtiles, (double*)out, w.err, selftest);
   return cudaGetLastError();
