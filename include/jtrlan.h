@@ -83,9 +83,15 @@ typedef struct {
  *   tol: convergence threshold on ||A x - lambda x|| with ||x|| = 1 (Algorithm 1, normal mode).
  *   which: JTRLAN_SMALLEST (smallest algebraic) or JTRLAN_LARGEST.
  *   precision: JTRLAN_FP64 -- plain FP64 arithmetic throughout.
- *     JTRLAN_MIXED_REORTH -- FP64 vectors, matvec, alpha/beta, Ritz solve and residuals; the
- *       reorthogonalisation against V and W = J V^* is classical Gram-Schmidt done twice with its
- *       inner products in FP32 (first update applied in FP64, second correction formed in FP32).
+ *     JTRLAN_MIXED_REORTH -- the basis V is stored as (hi, lo) FP32 pairs (about 48 significant
+ *       bits) and the three steps that plain FP64 spends on the FP64 pipe run in compensated FP32
+ *       ("double-float": exact FMA-split products, TwoSum-carried sums): the stencil product A v_j
+ *       (on (hi, lo) links, or on the complex64 links themselves when dtype is JTRLAN_C64, which
+ *       are exact in FP32; a dense operator keeps the FP64 product), the Gram-Schmidt passes
+ *       against V and W = J V^*, and the restart rotation V_m Z (on the tensor cores by exact BF16
+ *       digit splitting with FP32 accumulation in tensor memory when m <= 320 and rotate_simt is 0,
+ *       else on the CUDA cores).  The vector y being orthogonalised, alpha/beta, the norms and the
+ *       sqrt(2) test, the Ritz solve, the rotated Ritz vectors and the true residuals are FP64.
  *     JTRLAN_MIXED -- an FP32 phase (matvec, Gram-Schmidt and rotation in FP32; alpha/beta, Ritz
  *       solve and residual norms in FP64) run to max(tol, 1e-5 max|t|), then the JTRLAN_MIXED_REORTH
  *       solve started from the normalised sum of the FP32 Ritz vectors, run to tol.
@@ -147,6 +153,12 @@ typedef struct {
   int invert;         /* nonzero: Algorithm 1's invert mode (see below) */
   double cg_tol;      /* invert mode: relative residual ||b - A x|| / ||b|| of each CG solve (0: 1e-12) */
   int cg_max_iter;    /* invert mode: iterations per CG solve before JTRLAN_ENOCONV (0: 10000) */
+  int gs_split;       /* nonzero: the Gram-Schmidt part of every Lanczos step runs as separate kernel
+                         launches (first pass, reduction, update, later passes, normalisation) instead
+                         of one cooperative launch.  The library takes this path by itself where a
+                         cooperative launch is unavailable or one block's rows do not fit shared
+                         memory; the switch exists so that the path can be exercised on any size.
+                         Same arithmetic and results up to summation order. */
 } jtrlan_params;
 
 /* Counters of the last solve (Sec. 3 counts only the Lanczos-step products as N_MV). */
@@ -245,25 +257,31 @@ jtrlan_status jtrlan_damped_step(const double* tau, int count, int degree, float
  * The paper has no counterpart to this call; it exists for callers that cannot call cudaMalloc --
  * an application whose own caching allocator already holds the device memory it may use, code
  * that must not let cudaMalloc's implicit synchronisation stall other streams, or a plug-in given
- * no allocation rights.  It computes res[i] = ||A x_i - lambda[i] x_i|| (the true residual that
- * Algorithm 1 tests) for the ncols columns x_i of X, with the same kernels as the solver's
- * convergence check, and allocates nothing: its scratch lives in one static device array of
- * 8 * JTRLAN_NOALLOC_MAX_PARTIALS + 20 * JTRLAN_NOALLOC_MAX_COLS bytes (about 2 MiB) that every GPU
- * which loads the library holds until the process exits.
+ * no allocation rights.  It computes res[i] = ||A x_i - lambda[i] x_i|| for the ncols columns x_i
+ * of X, with the same kernels as the solver's convergence check, and allocates nothing: its
+ * scratch lives in one static device array of 8 * JTRLAN_NOALLOC_MAX_PARTIALS + 20 *
+ * JTRLAN_NOALLOC_MAX_COLS bytes (about 2 MiB) that every GPU which loads the library holds until the
+ * process exits.
  *   op: the operator; dtype must be JTRLAN_C128 and a11/a12 or U/W must be DEVICE pointers (no
  *     copy or conversion is made).  X: device, n x ncols complex128, column-major with leading
  *     dimension ldx >= n.  lambda: host, ncols doubles.  res: host, ncols doubles (written).
- *   cuda_stream: the stream to run on (NULL = legacy default); the call synchronises it.
+ *   cuda_stream: the stream to run on (NULL = legacy default); the call synchronises it.  It copies
+ *     from pageable host memory and synchronises, so it may not be made on a stream that is being
+ *     captured into a CUDA graph: that returns JTRLAN_EINVAL before anything is enqueued.
  * Limits: ncols <= JTRLAN_NOALLOC_MAX_COLS and ncols * B <= JTRLAN_NOALLOC_MAX_PARTIALS, where B is
  *   the number of blocks of one product (stencil: ceil(64 ceil(3 V / 8) / 256), which is
  *   ceil(24 V / 256) when V is a multiple of 8; dense: ceil((n/2) / 8)).
  *   Larger requests fail with JTRLAN_EINVAL and a message naming the limit: split the columns.
  * The first call on a device looks up the array's device address there (cudaGetSymbolAddress with
- * that device current); make that first call before any stream capture on the device.
+ * that device current) and caches it for the life of the process; after a cudaDeviceReset (or any
+ * other reset of the device's primary context) that address is stale, so do not use this call on a
+ * device that has been reset in the same process.
  * All calls on a device share the one array, and every call overwrites all of it that it reads,
  * so nothing carries over between calls; calls whose GPU work overlaps (on different streams or
- * host threads) race on it and must be serialised by the caller.
- * Errors: JTRLAN_EINVAL (null pointers, sizes beyond the limits, unsupported dtype), JTRLAN_ECUDA. */
+ * host threads) race on it and must be serialised by the caller.  When the call fails after it has
+ * enqueued work, it waits for that work before returning, so a retry does not race with it.
+ * Errors: JTRLAN_EINVAL (null pointers, sizes beyond the limits, unsupported dtype, a capturing
+ * stream), JTRLAN_ECUDA. */
 #define JTRLAN_NOALLOC_MAX_PARTIALS 262144
 #define JTRLAN_NOALLOC_MAX_COLS 1024
 jtrlan_status jtrlan_residual_norms_noalloc(const jtrlan_operator* op, const void* X, int64_t ldx,

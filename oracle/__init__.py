@@ -11,6 +11,7 @@ Contents:
                  brute-force dense assembly for small problems.
   trlan_jsym  -- Algorithm 1 (TRLAN-JSYM) and Algorithm 2 (LANCZOS_JSYM) in FP64,
                  in the paper's order and notation.
+  jacobi      -- the cyclic Jacobi eigensolver that diagonalises T_m in Algorithm 1.
   filter      -- polynomial filters p(A) (Chebyshev recurrence, damped step coefficients);
                  the paper has none, these are standard definitions.
   mlp         -- the 3-layer perceptron that predicts filter coefficients: forward pass,

@@ -19,6 +19,8 @@ R7  The sort that moves converged pairs to the top is stable and acts on the fir
     nev positions; the final output is sorted by eigenvalue (ascending for
     'smallest', descending for 'largest').
 R9  v_1 = (1, ..., 1)/sqrt(n) as in Algorithm 1 unless a start vector is given.
+R13 The eigendecomposition T_m = Z Lambda Z^T, for which the paper names no method, is the
+    oracle's own cyclic Jacobi (jacobi.py).
 R20 Invert mode (Algorithm 1's second branch): the Lanczos product is A^{-1} v_j, given as the
     function ``solve``; the wanted Ritz values of T are its largest (A's smallest); every restart
     takes c = ||A v_{m+1}|| with v_{m+1} the last Lanczos vector, and ev(i) = 1/lambda_i,
@@ -28,6 +30,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from .jacobi import jacobi_eigh
 from .jsym import pair
 
 
@@ -119,7 +122,7 @@ def trlan_jsym(matvec, n, nev, m, mwin, tol, which="smallest", v1=None, max_rest
         if on_lanczos is not None:
             on_lanczos(V, T, k, m)
         beta_m = T[m, m - 1]
-        lam, Z = np.linalg.eigh(T[:m, :m])               # T_m = Z Lambda Z^T
+        lam, Z = jacobi_eigh(T[:m, :m])                  # T_m = Z Lambda Z^T (cyclic Jacobi, R13)
         order = np.argsort(-lam if largest_of_T else lam, kind="stable")
         lam, Z = lam[order], Z[:, order]                 # desired pairs first
         V[:, :m] = V[:, :m] @ Z                          # V_m := V_m Z_m

@@ -47,7 +47,7 @@ class jtrlan_params(ctypes.Structure):
                 ("filter_hi", ctypes.c_double), ("filter_final_degree", ctypes.c_int),
                 ("filter_final_coeffs", ctypes.c_void_p), ("plain_trlan", ctypes.c_int),
                 ("rotate_simt", ctypes.c_int), ("invert", ctypes.c_int), ("cg_tol", ctypes.c_double),
-                ("cg_max_iter", ctypes.c_int)]
+                ("cg_max_iter", ctypes.c_int), ("gs_split", ctypes.c_int)]
 
 
 class jtrlan_stats(ctypes.Structure):
@@ -341,7 +341,7 @@ def dense_operator(n, a11_ptr, a12_ptr, dtype=JTRLAN_C128) -> jtrlan_operator:
 def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_restarts=0,
            gs_max_passes=0, v1_ptr=None, check_jsym=0, profile=0, filter_coeffs=None, filter_window=None,
            filter_final_coeffs=None, plain_trlan=0, rotate_simt=0, invert=0, cg_tol=0.0,
-           cg_max_iter=0) -> jtrlan_params:
+           cg_max_iter=0, gs_split=0) -> jtrlan_params:
     """filter_coeffs / filter_final_coeffs: float64 arrays g_0..g_d (kept alive on the struct until
     create copies them); filter_window: (lo, hi)."""
     p = jtrlan_params()
@@ -354,6 +354,7 @@ def params(nev, m, mwin, tol, which=JTRLAN_SMALLEST, precision=JTRLAN_FP64, max_
     p.plain_trlan = int(plain_trlan)
     p.rotate_simt = int(rotate_simt)
     p.invert, p.cg_tol, p.cg_max_iter = int(invert), float(cg_tol), int(cg_max_iter)
+    p.gs_split = int(gs_split)
     if filter_coeffs is not None:
         import numpy as np
         g = np.ascontiguousarray(filter_coeffs, dtype=np.float64)

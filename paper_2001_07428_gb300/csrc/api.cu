@@ -474,6 +474,7 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
       }
     }
   }
+  if (prm->gs_split) c->coop64 = c->coop32 = c->coopdf = 0;   // the separate-launch Gram-Schmidt path
   const int nblk_max = std::max(c->gs_nblk, std::max(std::max(c->coop64, c->coop32), c->coopdf));
   JT_TRY(c->dalloc(&c->T, (size_t)(m + 1) * (m + 1) * sizeof(double)));
   JT_TRY(c->dalloc(&c->lam, (size_t)m * sizeof(double)));

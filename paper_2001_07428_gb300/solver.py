@@ -27,7 +27,7 @@ class JTRLan:
                  U=None, W=None, A11=None, A12=None, v1=None, max_restarts=0, gs_max_passes=0,
                  check_jsym=False, profile=False, precision="fp64", filter_coeffs=None, filter_window=None,
                  filter_final_coeffs=None, plain_trlan=False, links_dtype="c128", rotate_simt=False,
-                 invert=False, cg_tol=0.0, cg_max_iter=0, device="cuda"):
+                 invert=False, cg_tol=0.0, cg_max_iter=0, gs_split=False, device="cuda"):
         B.load()
         self.device = torch.device(device)
         self.stream = torch.cuda.current_stream(self.device)
@@ -61,7 +61,7 @@ class JTRLan:
                        profile=int(profile), filter_coeffs=filter_coeffs, filter_window=filter_window,
                        filter_final_coeffs=filter_final_coeffs, plain_trlan=int(plain_trlan),
                        rotate_simt=int(rotate_simt), invert=int(invert), cg_tol=cg_tol,
-                       cg_max_iter=cg_max_iter)
+                       cg_max_iter=cg_max_iter, gs_split=int(gs_split))
         self.ctx = B.jtrlan_create(op, prm, self.stream.cuda_stream)
         # jtrlan_create copied the operator; v1 is read at solve time, so it is kept alive.
 

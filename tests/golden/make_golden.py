@@ -1,6 +1,8 @@
 """Writes the stored expected values under tests/golden/ by running the CPU oracle only.
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [WORKLOAD ...]      (default: stencil_8x8x8x8)
+
+stencil_16x16x16x16 (n = 393,216, nev 50, m 120) takes about two hours of one core.
 
 Each file records the seeded workload it came from and the oracle's nev smallest
 eigenvalues (Algorithm 1 run to tol = 1e-12 on ||A x - lambda x||, ||x|| = 1), so that
@@ -47,4 +49,5 @@ def stencil_golden(name, tol=1e-12):
 
 
 if __name__ == "__main__":
-    stencil_golden("stencil_8x8x8x8")
+    for name in sys.argv[1:] or ["stencil_8x8x8x8"]:
+        stencil_golden(name)

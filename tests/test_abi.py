@@ -49,11 +49,12 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(jtrlan_operator), offsetof(jtrlan_operator, n),
          offsetof(jtrlan_operator, m0), offsetof(jtrlan_operator, a11), offsetof(jtrlan_operator, W));
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_params), offsetof(jtrlan_params, tol),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_params), offsetof(jtrlan_params, tol),
          offsetof(jtrlan_params, v1), offsetof(jtrlan_params, check_jsym), offsetof(jtrlan_params, profile),
          offsetof(jtrlan_params, filter_hi), offsetof(jtrlan_params, filter_final_coeffs),
          offsetof(jtrlan_params, plain_trlan), offsetof(jtrlan_params, rotate_simt),
-         offsetof(jtrlan_params, invert), offsetof(jtrlan_params, cg_tol), offsetof(jtrlan_params, cg_max_iter));
+         offsetof(jtrlan_params, invert), offsetof(jtrlan_params, cg_tol), offsetof(jtrlan_params, cg_max_iter),
+         offsetof(jtrlan_params, gs_split));
   printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(jtrlan_stats), offsetof(jtrlan_stats, n_restarts),
          offsetof(jtrlan_stats, solve_ms), offsetof(jtrlan_stats, n_launches), offsetof(jtrlan_stats, n_ritz_fallbacks),
          offsetof(jtrlan_stats, n_matvec_fp32), offsetof(jtrlan_stats, n_matvec_inner),
@@ -72,7 +73,8 @@ int main(void) {
     assert got[0] == [ctypes.sizeof(O), O.n.offset, O.m0.offset, O.a11.offset, O.W.offset]
     assert got[1] == [ctypes.sizeof(P), P.tol.offset, P.v1.offset, P.check_jsym.offset, P.profile.offset,
                       P.filter_hi.offset, P.filter_final_coeffs.offset, P.plain_trlan.offset,
-                      P.rotate_simt.offset, P.invert.offset, P.cg_tol.offset, P.cg_max_iter.offset]
+                      P.rotate_simt.offset, P.invert.offset, P.cg_tol.offset, P.cg_max_iter.offset,
+                      P.gs_split.offset]
     assert got[2] == [ctypes.sizeof(S), S.n_restarts.offset, S.solve_ms.offset, S.n_launches.offset,
                       S.n_ritz_fallbacks.offset, S.n_matvec_fp32.offset, S.n_matvec_inner.offset,
                       S.n_cg_iters.offset]
