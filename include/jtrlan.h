@@ -99,8 +99,9 @@ typedef struct {
  *   max_restarts: bound on outer iterations (N_conv); 0 selects 1000.
  *   gs_max_passes: bound on Gram-Schmidt passes per Lanczos step (Algorithm 2 has none);
  *     0 selects 3.
- *   v1: optional start vector (n complex in the operator's dtype, host or device); NULL gives
- *     v1 = (1, ..., 1)/sqrt(n) as in Algorithm 1.  It is normalised by the library.
+ *   v1: optional start vector (n complex128 numbers, whatever the operator's dtype; host or
+ *     device), read by every jtrlan_solve; NULL gives v1 = (1, ..., 1)/sqrt(n) as in Algorithm 1.
+ *     It is normalised by the library.
  *   check_jsym: if nonzero, jtrlan_create tests Lemma 1, |(J v*)^H A v| <= 1e-10 ||A v|| ||v||,
  *     on a fixed pseudo-random v and fails with JTRLAN_ENOTJSYM otherwise.
  *   profile: if nonzero, jtrlan_solve brackets every kernel launch with CUDA events on the context
@@ -242,9 +243,24 @@ jtrlan_status jtrlan_apply_filter(jtrlan_ctx* ctx, const void* x, void* y);
  * context's working precision (FP32 for JTRLAN_MIXED), then the Rayleigh-Ritz values of the
  * steps x steps tridiagonal in FP64.  *lo = theta_min - |beta_steps z_{steps,min}| (the smallest
  * Ritz value less its residual bound: an estimate of lambda_min), *hi = theta_max + beta_steps (an
- * estimate, not a guarantee, of an upper bound of lambda_max).  2 <= steps <= m.  Synchronises the context stream.  Errors: JTRLAN_EINVAL,
+ * estimate, not a guarantee, of an upper bound of lambda_max).  2 <= steps <= m.  Synchronises the
+ * context stream.  Afterwards jtrlan_get_profile describes this call (its launches) until the next
+ * solve.  Errors: JTRLAN_EINVAL,
  * JTRLAN_EBREAKDOWN, JTRLAN_ECUDA. */
 jtrlan_status jtrlan_bounds(jtrlan_ctx* ctx, int steps, double* lo, double* hi);
+
+/* Sets (or replaces) the certifying phase's filter of a context: the same as creating it with
+ * filter_final_degree = degree, filter_final_coeffs = coeffs (host, degree + 1 Chebyshev coefficients
+ * g_0..g_degree, copied) and the window [lo, hi], so that a later jtrlan_solve runs Algorithm 1 on
+ * B = p(A) with every pair certified by the true residual of A (see jtrlan_params).  The window is
+ * shared with the FP32-phase filter of JTRLAN_MIXED.  It lets one context serve a filter chosen per
+ * solve (the learned filter: jtrlan_bounds on this context, the network, then this call) without
+ * copying the operator again.  The first call on a context created without a certifying filter
+ * allocates that phase's buffers (four vectors); later calls only copy coefficients.  Clears the
+ * results of the last solve (jtrlan_pairs returns JTRLAN_ESTATE until the next solve).
+ * Errors: JTRLAN_EINVAL (null, degree outside 1..1024, lo >= hi, a non-finite coefficient, an
+ * invert-mode context), JTRLAN_ENOMEM. */
+jtrlan_status jtrlan_set_filter(jtrlan_ctx* ctx, int degree, const double* coeffs, double lo, double hi);
 
 /* Jackson-damped Chebyshev coefficients of the step [x <= tau_i] (Jackson damping as in Weisse et
  * al., Rev. Mod. Phys. 78, 275 (2006), N = degree + 1 moments), the targets of the learned filter:

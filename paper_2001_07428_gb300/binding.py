@@ -26,7 +26,7 @@ EXPORTED = ["jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jt
             "jtrlan_batch_results", "jtrlan_batch_vectors", "jtrlan_batch_destroy", "jtrlan_apply_filter", "jtrlan_bounds",
             "jtrlan_damped_step", "jtrlan_mlp_param_count", "jtrlan_mlp_create", "jtrlan_mlp_get_params",
             "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train",
-            "jtrlan_mlp_destroy", "jtrlan_rotate_df"]
+            "jtrlan_mlp_destroy", "jtrlan_rotate_df", "jtrlan_set_filter"]
 NOALLOC_MAX_PARTIALS = 262144   # JTRLAN_NOALLOC_MAX_PARTIALS
 NOALLOC_MAX_COLS = 1024         # JTRLAN_NOALLOC_MAX_COLS
 
@@ -138,6 +138,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jtrlan_batch_destroy.restype = None
     lib.jtrlan_apply_filter.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.jtrlan_bounds.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)]
+    lib.jtrlan_set_filter.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
     lib.jtrlan_damped_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.jtrlan_mlp_param_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.jtrlan_mlp_param_count.restype = ctypes.c_int64
@@ -159,7 +160,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
               "jtrlan_batch_tune", "jtrlan_batch_solve", "jtrlan_batch_results", "jtrlan_batch_vectors",
               "jtrlan_apply_filter", "jtrlan_bounds", "jtrlan_damped_step", "jtrlan_mlp_create", "jtrlan_mlp_get_params",
               "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train",
-              "jtrlan_rotate_df"):
+              "jtrlan_rotate_df", "jtrlan_set_filter"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -264,6 +265,14 @@ def jtrlan_bounds(ctx, steps: int):
     lo, hi = ctypes.c_double(), ctypes.c_double()
     _check(load().jtrlan_bounds(ctx, int(steps), ctypes.byref(lo), ctypes.byref(hi)))
     return lo.value, hi.value
+
+
+def jtrlan_set_filter(ctx, coeffs, window):
+    """The certifying phase's filter of a context: Chebyshev coefficients g_0..g_d on [lo, hi]."""
+    import numpy as np
+    g = np.ascontiguousarray(coeffs, dtype=np.float64)
+    _check(load().jtrlan_set_filter(ctx, len(g) - 1, g.ctypes.data_as(ctypes.c_void_p), float(window[0]),
+                                    float(window[1])))
 
 
 def jtrlan_damped_step(tau_ptr: int, count: int, degree: int, out_ptr: int, stream: int = 0):

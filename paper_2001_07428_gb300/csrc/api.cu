@@ -275,6 +275,24 @@ jtrlan_status validate(const jtrlan_operator* op, const jtrlan_params* p) {
   return JTRLAN_OK;
 }
 
+// Turns the final phase (FP64, or double-float in the mixed forms) into the certifying filtered phase
+// on B = p(A) with coefficients g_0..g_degree: buffers on the first call, coefficients every call.
+jtrlan_status setup_certify(jtrlan_ctx* c, const double* coeffs, int degree) {
+  Phase& ph = c->mixed ? c->pdf : c->p64;
+  if (!ph.certify) {
+    ph.filtered = true;
+    ph.certify = true;
+    ph.which = JTRLAN_LARGEST;
+    for (int b = 0; b < 3; ++b) JT_TRY(c->dalloc(&ph.fbuf[b], (size_t)c->n * sizeof(double2)));
+    JT_TRY(c->dalloc(&ph.fbuf[3], (size_t)c->n * sizeof(float4)));
+    const int nb = std::max(cheb_blocks(c->n), ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk);
+    JT_TRY(c->dalloc(&ph.alpha_part, (size_t)nb * sizeof(double2)));
+    JT_TRY(c->dalloc(&ph.resid_part, (size_t)std::max(nb, ph.mv_nblk * c->nev) * sizeof(double)));
+  }
+  ph.fcoef.assign(coeffs, coeffs + degree + 1);
+  return JTRLAN_OK;
+}
+
 jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, void* stream, jtrlan_ctx** out) {
   JT_TRY(validate(op, prm));
   jtrlan_ctx* c = new (std::nothrow) jtrlan_ctx();
@@ -418,18 +436,8 @@ jtrlan_status create_impl(const jtrlan_operator* op, const jtrlan_params* prm, v
   }
   c->fc = 0.5 * (prm->filter_lo + prm->filter_hi);
   c->fe = 0.5 * (prm->filter_hi - prm->filter_lo);
-  if (prm->filter_final_degree > 0) {   // the certifying phase on B = p(A), judged by A's residuals
-    Phase& ph = c->mixed ? c->pdf : c->p64;
-    ph.filtered = true;
-    ph.certify = true;
-    ph.which = JTRLAN_LARGEST;
-    ph.fcoef.assign(prm->filter_final_coeffs, prm->filter_final_coeffs + prm->filter_final_degree + 1);
-    for (int b = 0; b < 3; ++b) JT_TRY(c->dalloc(&ph.fbuf[b], (size_t)c->n * sizeof(double2)));
-    JT_TRY(c->dalloc(&ph.fbuf[3], (size_t)c->n * sizeof(float4)));
-    const int nb = std::max(cheb_blocks(c->n), ph.dfmv ? matvec_df_blocks(ph.opdf) : ph.mv_nblk);
-    JT_TRY(c->dalloc(&ph.alpha_part, (size_t)nb * sizeof(double2)));
-    JT_TRY(c->dalloc(&ph.resid_part, (size_t)std::max(nb, ph.mv_nblk * c->nev) * sizeof(double)));
-  }
+  if (prm->filter_final_degree > 0)   // the certifying phase on B = p(A), judged by A's residuals
+    JT_TRY(setup_certify(c, prm->filter_final_coeffs, prm->filter_final_degree));
   {  // cooperative Gram-Schmidt step: its own row partition, one row block per resident CTA
     int dev = 0, nsm = 0;
     JT_CUDA(cudaGetDevice(&dev));
@@ -994,6 +1002,7 @@ jtrlan_status bounds_impl(jtrlan_ctx* c, int steps, double* lo, double* hi) {
   const int64_t n = c->n;
   const int ldt = c->m + 1;
   c->prof.used = 0;
+  for (int t = 0; t < K_NTAGS; ++t) { c->prof.ms[t] = 0; c->nl[t] = 0; c->work[t] = 0; }
   JT_CUDA(cudaMemsetAsync(c->st, 0, sizeof(StepState), s));
   JT_CUDA(cudaMemsetAsync(c->T, 0, (size_t)ldt * ldt * sizeof(double), s));
   const uint64_t seed = 0xb07d5ull;
@@ -1045,7 +1054,6 @@ jtrlan_status solve_impl(jtrlan_ctx* c, jtrlan_stats* stats_out) {
   std::vector<double> ev, res;
   int icnv = 0;
   jtrlan_status st = JTRLAN_OK;
-  if (c->prm.v1 && c->opd.dtype != JTRLAN_C128) return fail(JTRLAN_EINVAL, "v1 must be complex128");
   if (c->prm.precision == JTRLAN_MIXED) {
     // FP32 phase: matvec, Gram-Schmidt and rotation in FP32, alpha/beta and Ritz in FP64, to the
     // tolerance max(tol, 1e-5 max|t|) that FP32 vectors can certify.
@@ -1246,6 +1254,24 @@ jtrlan_status jtrlan_rotate_df(const void* V, int64_t n, int m, const double* Z,
   if (e != cudaSuccess) return fail(JTRLAN_ECUDA, std::string("tensor-core rotation: ") + cudaGetErrorString(e));
   if (herr != 0)
     return fail(JTRLAN_ETIMEOUT, "tensor-core rotation: a bounded wait ran out (code " + std::to_string(herr) + ")");
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_set_filter(jtrlan_ctx* c, int degree, const double* coeffs, double lo, double hi) {
+  if (!c || !coeffs) return fail(JTRLAN_EINVAL, "null argument");
+  if (degree < 1 || degree > 1024) return fail(JTRLAN_EINVAL, "need 1 <= degree <= 1024");
+  if (!(lo < hi)) return fail(JTRLAN_EINVAL, "need lo < hi");
+  if (c->invert) return fail(JTRLAN_EINVAL, "invert mode takes no filter");
+  for (int k = 0; k <= degree; ++k)
+    if (!std::isfinite(coeffs[k])) return fail(JTRLAN_EINVAL, "filter coefficients must be finite");
+  JT_TRY(setup_certify(c, coeffs, degree));
+  c->prm.filter_final_degree = degree;
+  c->prm.filter_final_coeffs = nullptr;   // the caller's array is not kept
+  c->prm.filter_lo = lo;
+  c->prm.filter_hi = hi;
+  c->fc = 0.5 * (lo + hi);
+  c->fe = 0.5 * (hi - lo);
+  c->solved = false;
   return JTRLAN_OK;
 }
 

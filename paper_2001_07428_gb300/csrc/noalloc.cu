@@ -9,7 +9,9 @@
 //
 // The array is a module global: every GPU that loads the library holds it until the process
 // exits, and all calls on a device share it.  Its device address is looked up once per device
-// (cudaGetSymbolAddress with that device current) on the first call there.
+// (cudaGetSymbolAddress with that device current) on the first call there and cached; a
+// cudaDeviceReset (or any other reset of the primary context) leaves that cached address stale, so
+// the entry point must not be used on a device after such a reset in the same process.
 #include <cstdio>
 #include <mutex>
 
@@ -105,22 +107,34 @@ extern "C" jtrlan_status jtrlan_residual_norms_noalloc(const jtrlan_operator* op
   if ((int64_t)ncols * nblk > kPartials)
     return noalloc_fail(JTRLAN_EINVAL,
                         "ncols * blocks per product exceeds JTRLAN_NOALLOC_MAX_PARTIALS; pass fewer columns per call");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the call copies from pageable host memory and synchronises the stream, neither of which a
+  // capturing stream allows: refuse before anything is enqueued
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return noalloc_fail(JTRLAN_ECUDA, "cudaStreamIsCapturing", e);
+  if (cap != cudaStreamCaptureStatusNone)
+    return noalloc_fail(JTRLAN_EINVAL, "the stream is being captured; this call cannot be captured");
   NoAllocScratch* sc = nullptr;
   jtrlan_status st = scratch_on_current_device(&sc);
   if (st != JTRLAN_OK) return st;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  cudaError_t e;
+  // once work is enqueued, an error return first waits for that work (ignoring its status), so that
+  // no kernel of this call still uses the shared array when the caller retries
+  auto fail_after_enqueue = [&](const char* what, cudaError_t err) {
+    cudaStreamSynchronize(s);
+    return noalloc_fail(JTRLAN_ECUDA, what, err);
+  };
   iota_kernel<<<1, 256, 0, s>>>(sc->cols, ncols);
   if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_fail(JTRLAN_ECUDA, "iota launch", e);
   e = cudaMemcpyAsync(sc->lambda, lambda, ncols * sizeof(double), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return noalloc_fail(JTRLAN_ECUDA, "copy of lambda", e);
+  if (e != cudaSuccess) return fail_after_enqueue("copy of lambda", e);
   e = launch_matvec<double>(o, (const double2*)X, nullptr, MV_RESID, sc->partials, sc->cols, sc->lambda, ncols, ldx,
                             nullptr, s);
-  if (e != cudaSuccess) return noalloc_fail(JTRLAN_ECUDA, "residual kernel", e);
+  if (e != cudaSuccess) return fail_after_enqueue("residual kernel", e);
   e = launch_reduce_norms(sc->partials, nblk, ncols, sc->norms, s);
-  if (e != cudaSuccess) return noalloc_fail(JTRLAN_ECUDA, "reduction kernel", e);
+  if (e != cudaSuccess) return fail_after_enqueue("reduction kernel", e);
   e = cudaMemcpyAsync(res, sc->norms, ncols * sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return noalloc_fail(JTRLAN_ECUDA, "copy of the norms", e);
+  if (e != cudaSuccess) return fail_after_enqueue("copy of the norms", e);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return noalloc_fail(JTRLAN_ECUDA, "stream synchronisation", e);
   return JTRLAN_OK;

@@ -145,4 +145,7 @@ WORKLOADS = {
                             nev=20, m=60, mwin=30),
     "stencil_16x16x16x16": dict(kind="stencil", dims=(16, 16, 16, 16), m0=8.5, kappa=0.3, seed=1,
                                 nev=50, m=120, mwin=60),
+    # the largest lattice: links stored in complex64, as its workload states
+    "stencil_24x24x24x48": dict(kind="stencil", dims=(24, 24, 24, 48), m0=8.5, kappa=0.3, seed=1,
+                                nev=100, m=200, mwin=100, links="c64"),
 }

@@ -142,6 +142,18 @@ def learned_filter(net: FilterNet, U, W, dims, m0, kappa, nev, device="cuda"):
     return g, window(lo, hi), f
 
 
+def filter_on_context(net: FilterNet, ctx, m0, kappa, nev, sites):
+    """The learned filter for the operator of an existing context, set on that context: jtrlan_bounds
+    on the context itself, network inference, jtrlan_set_filter.  Returns (coefficients, window,
+    features); the next jtrlan_solve of the context runs on B = p(A)."""
+    lo, hi = B.jtrlan_bounds(ctx, BOUNDS_STEPS)
+    f = features(lo, hi, m0, kappa, nev, sites)
+    g = net.predict(f[None, :])[0]
+    win = window(lo, hi)
+    B.jtrlan_set_filter(ctx, g, win)
+    return g, win, f
+
+
 def solve_learned(net: FilterNet, U, W, dims, m0, kappa, nev, m, mwin, tol, device="cuda", **kw):
     """J-TRLan (JTRLAN_MIXED_REORTH) on B = p(A) with the network's filter, every pair certified by the
     true residual of A.  Falls back to the unfiltered solve if the filtered one fails.

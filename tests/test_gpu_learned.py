@@ -80,3 +80,41 @@ def test_learned_filter_gains_over_the_unfiltered_method(LF):
         assert np.linalg.norm(r) < tol
     assert st["n_restarts"] < st0["n_restarts"] / 2
     assert t_learned < 0.5 * t_plain, (t_learned, t_plain)
+
+
+def test_filter_set_on_a_context_matches_one_created_with_it(LF):
+    """jtrlan_set_filter on a context created without a filter (bounds on that context, then the
+    network) gives the same solve, bit for bit, as a context created with those coefficients; the
+    eigenvalues agree with the unfiltered solve; a second call replaces the filter and clears the
+    pairs until the next solve."""
+    from paper_2001_07428_gb300 import binding as B
+    from paper_2001_07428_gb300.solver import JTRLan
+    dims, nev, m, mwin, tol = (8, 8, 8, 8), 20, 60, 30, 1e-8
+    U, W = inputs.stencil_links(dims, 1)
+    kw = dict(kind="stencil", dims=dims, m0=8.5, kappa=0.3, U=U, W=W, nev=nev, m=m, mwin=mwin, tol=tol,
+              precision="mixed_reorth", device="cuda:0")
+    net = LF.FilterNet.load()
+    s = JTRLan(**kw)
+    g, win, _ = LF.filter_on_context(net, s.ctx, 8.5, 0.3, nev, 4096)
+    s.solve()
+    ev1, X1, res1 = s.pairs()
+    ref = JTRLan(filter_final_coeffs=g, filter_window=win, **kw)
+    ref.solve()
+    ev0, _, _ = ref.pairs()
+    ref.close()
+    assert np.array_equal(ev1, ev0)
+    plain = JTRLan(**kw)
+    plain.solve()
+    evp, _, _ = plain.pairs()
+    plain.close()
+    assert (np.abs(ev1 - evp) / np.abs(evp)).max() < 1e-10
+    assert (res1 < tol).all()
+    g2, win2, _ = LF.filter_on_context(net, s.ctx, 8.5, 0.3, nev, 4096)
+    assert np.array_equal(g2, g) and win2 == win        # bounds are deterministic
+    with pytest.raises(B.JTRLanError) as ei:
+        s.pairs()
+    assert ei.value.status == B.JTRLAN_ESTATE
+    s.solve()
+    ev2, _, _ = s.pairs()
+    s.close()
+    assert np.array_equal(ev2, ev1)
