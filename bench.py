@@ -49,7 +49,14 @@ from paper_2001_07428_gb300 import inputs  # noqa: E402
 
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 TOL = 1e-8
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max clock
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max clock
+
+
+def fp64_peak_tflops(peaks=None):
+    """The FP64 FMA peak: measured by the library's FMA loop when `peaks` holds it, else derived."""
+    if peaks and peaks.get("fp64_fma_tflops"):
+        return peaks["fp64_fma_tflops"], "measured: FP64 FMA loop (jtrlan_measure_peaks)"
+    return FP64_PEAK_DERIVED, "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -533,7 +540,8 @@ def batched_oracle_sample(picks):
     return time.perf_counter() - t0
 
 
-def batched_dense(B, torch, stream, steps, warmup, cpu=True, count=None, shape=None, forms=("fp64", "mixed_reorth")):
+def batched_dense(B, torch, stream, steps, warmup, cpu=True, count=None, shape=None, forms=("fp64", "mixed_reorth"),
+                  peaks=None):
     """The batch in one persistent launch per solve (CUDA-graph replay, autotuned launch shape), plain
     FP64 and the compensated-FP32 form; K timed solves each after W warm-up solves.  Inputs (408 MB of
     packed blocks) exceed L2.  Roofline: algorithmic matvec work (32 flop and 32 bytes per (row pair,
@@ -590,7 +598,14 @@ def batched_dense(B, torch, stream, steps, warmup, cpu=True, count=None, shape=N
              "n_gs_passes": int(st["n_gs_passes"]), "n_ritz_fallbacks": int(st["n_ritz_fallbacks"]),
              "phase_share": {k: round(v, 4) for k, v in sp["phase_frac"].items()},
              "matvec_tflops": round(flop / t / 1e12, 4), "matvec_gbs": round(byts / t / 1e9, 1)}
-        e["frac_of_fp64_peak"] = round(e["matvec_tflops"] / FP64_PEAK_TFLOPS, 4)
+        fp64_peak, fp64_src = fp64_peak_tflops(peaks)
+        if name == "fp64":   # FP64-pipe-bound: the products' FP64 flops against the measured FP64 FMA peak
+            e["bound"] = "alu (FP64 pipe)"
+            e["frac_of_fp64_peak"] = round(e["matvec_tflops"] / fp64_peak, 4)
+            e["fp64_peak_tflops"], e["fp64_peak_source"] = round(fp64_peak, 3), fp64_src
+        else:                # compensated FP32: FP32-issue-bound; matvec_tflops counts FP64-equivalent flops
+            e["bound"] = "alu (FP32 issue; compensated arithmetic)"
+            e["matvec_tflops_fp64_equivalent"] = e.pop("matvec_tflops")
         e["frac_of_hbm"] = round(e["matvec_gbs"] / hbm, 4)
         out[name] = e
     if len(forms) == 2:
@@ -687,6 +702,8 @@ def run_gb300(args, rank, world, local_rank):
     B.load()
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    peaks = B.jtrlan_measure_peaks(torch.cuda.current_stream(dev).cuda_stream)
+    fp64_peak, fp64_src = fp64_peak_tflops(peaks)
     w = workload(args.workload)
     dims = w["dims"]
     U, W = inputs.stencil_links(dims, w["seed"])
@@ -794,17 +811,17 @@ def run_gb300(args, rank, world, local_rank):
     hbm_peak, hbm_src = measured_peaks()
     if "tflops" in kernels[dom]:
         ach = kernels[dom]["tflops"]
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": round(FP64_PEAK_TFLOPS, 3),
-                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": round(fp64_peak, 3),
+                "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4),
                 "traffic": ncu_traffic(dom, args.workload),
-                "peak_source": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+                "peak_source": fp64_src}
     else:
         roof = {"kernel": dom, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
     mvk = kernels.get("matvec", {})
     stencil = {"gbs": mvk.get("gbs"), "frac_of_hbm": round(mvk["gbs"] / hbm_peak, 4) if mvk.get("gbs") else None,
                "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src, "tflops": mvk.get("tflops"),
-               "frac_of_fp64": round(mvk["tflops"] / FP64_PEAK_TFLOPS, 4) if mvk.get("tflops") else None,
+               "frac_of_fp64": round(mvk["tflops"] / fp64_peak, 4) if mvk.get("tflops") else None,
                "note": "8^4 in c128 is L2-resident (5.5 MB) and FP64-ALU-bound; GB/s counts 84 words/site"}
 
     # ---- end to end through the C ABI from pinned host buffers
@@ -849,7 +866,7 @@ def run_gb300(args, rank, world, local_rank):
     if not args.no_learned:
         line["learned_filter"] = learned_compare(B, torch, "16x16x16x16", with_fp64=False)
     if not args.no_batched:
-        line["batched_dense"] = batched_dense(B, torch, stream, args.steps, args.warmup,
+        line["batched_dense"] = batched_dense(B, torch, stream, args.steps, args.warmup, peaks=peaks,
                                               cpu=world == 1 and not args.no_cpu_baseline)
     if world == 1 and not args.no_cpu_baseline:
         # the oracle's own product count for the whole solve (it re-verifies locked pairs every
@@ -867,14 +884,17 @@ HEADLINE = "stencil_24x24x24x48"
 FP32_LANES = 152 * 128          # SMs x FP32 lanes per SM (4 partitions x 32)
 
 
-def fp32_peak_ops():
-    """FP32 issue peak in operations/s (one FMA, add or multiply per lane per clock) at the measured
-    maximum SM clock."""
+def fp32_peak_ops(peaks=None):
+    """FP32 issue peak in operations/s (one FMA, add or multiply per lane per clock): measured by the
+    library's FMA loop when `peaks` holds it (FMA counted as one operation), else 152 SMs x 128 lanes
+    at the maximum SM clock.  Returns (ops/s, source)."""
+    if peaks and peaks.get("fp32_fma_tflops"):
+        return peaks["fp32_fma_tflops"] / 2 * 1e12, "measured: FP32 FMA loop (jtrlan_measure_peaks), one op per FMA"
     mhz = 2070.0
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
-    return FP32_LANES * mhz * 1e6
+    return FP32_LANES * mhz * 1e6, "derived: 152 SMs x 128 lanes x max SM clock"
 
 
 # Algorithmic work per unit of each kernel class of the learned-filter solve (units from the library's
@@ -895,7 +915,7 @@ LEARNED_UNIT_WORK = {
 }
 
 
-def learned_roofline(kernels, workload_name):
+def learned_roofline(kernels, workload_name, peaks=None):
     """The roofline object for the kernel class with the largest device time of a profiled step."""
     hbm, hsrc = measured_peaks()
     dom = max((k for k in kernels if k in LEARNED_UNIT_WORK), key=lambda k: kernels[k]["ms"])
@@ -908,12 +928,11 @@ def learned_roofline(kernels, workload_name):
         out.update(achieved=round(ach, 1), peak=hbm, unit="GB/s", frac=round(ach / hbm, 4),
                    peak_source=f"{hsrc} (MEASURED_PEAKS.json hbm_gbs)")
     elif bound == "alu":
-        peak = fp32_peak_ops() / 1e12
+        peak, psrc = fp32_peak_ops(peaks)
+        peak /= 1e12
         ach = e["work"] * per_unit / sec / 1e12
-        out.update(achieved=round(ach, 2), peak=round(peak, 2), unit="TFLOP/s", frac=round(ach / peak, 4),
-                   peak_source="FP32 issue rate: 152 SMs x 128 lanes x measured max SM clock (one op per "
-                               "lane per clock; an FMA counted as one op)",
-                   work="FP32 ops of the compensated arithmetic as written, per lattice site")
+        out.update(achieved=round(ach, 2), peak=round(peak, 2), unit="Tops/s", frac=round(ach / peak, 4),
+                   peak_source=psrc, work="FP32 ops of the compensated arithmetic as written, per lattice site")
     else:
         peak, src = bf16_peak()
         ach = e["work"] * per_unit / sec / 1e12
@@ -1005,6 +1024,7 @@ def run_headline(args, rank, world, local_rank):
     B.load()
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    peaks = B.jtrlan_measure_peaks(torch.cuda.current_stream(dev).cuda_stream)
     name = args.workload
     w = workload(name)
     dims, nev, m, mwin = w["dims"], w["nev"], w["m"], w["mwin"]
@@ -1062,7 +1082,7 @@ def run_headline(args, rank, world, local_rank):
     step(ctxp)
     kernels = profile_table(B.jtrlan_get_profile(ctxp))
     B.jtrlan_destroy(ctxp)
-    roof = learned_roofline(kernels, name)
+    roof = learned_roofline(kernels, name, peaks)
 
     # ---- the FP32 stencil matvec of this lattice against the measured HBM peak
     stencil = stencil_apply_roofline(dims)
@@ -1134,6 +1154,7 @@ def run_headline(args, rank, world, local_rank):
             "step_s": [round(x, 4) for x in times], "max_residual": float(res_l.max()),
             "filter": {"degree": len(g) - 1, "window": list(win), "cut_tau": float(np.cos(np.pi * (1 - g[0])))},
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "kernels": kernels,
+            "measured_peaks": {k: round(v, 3) for k, v in peaks.items()},
             "stencil_fp32": stencil, "vs_plain_fp64": fp64,
             "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "steps": args.e2e_steps},
@@ -1201,6 +1222,49 @@ def run_reference_headline(args, rank, world):
 
 
 
+def one_step(args):
+    """One step of the learned-filter form on a workload (for profilers): context, bounds, inference,
+    set_filter, solve; prints the step's time and counters.  --gs-split forces the separate-launch
+    Gram-Schmidt; --max-restarts bounds the solve (a bounded solve that stops early still exits 0)."""
+    import ctypes
+
+    import torch
+
+    from paper_2001_07428_gb300 import binding as B
+    from paper_2001_07428_gb300 import learned_filter as LF
+    B.load()
+    dev = torch.device("cuda", 0)
+    w = workload(args.one_step)
+    dims, nev, m, mwin = w["dims"], w["nev"], w["m"], w["mwin"]
+    vol = inputs.lattice_volume(dims)
+    U, W = inputs.stencil_links(dims, w["seed"])
+    U, W = U.astype(np.complex64), W.astype(np.complex64)
+    Ud, Wd = torch.from_numpy(U).to(dev), torch.from_numpy(W).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    op = B.stencil_operator(dims, w["m0"], w["kappa"], Ud.data_ptr(), Wd.data_ptr(), dtype=B.JTRLAN_C64)
+    net = LF.FilterNet.load(device=dev)
+    ctx = B.jtrlan_create(op, B.params(nev, m, mwin, TOL, precision=B.JTRLAN_MIXED_REORTH,
+                                       max_restarts=args.max_restarts, gs_split=int(args.gs_split)),
+                          stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g, win, _ = LF.filter_on_context(net, ctx, w["m0"], w["kappa"], nev, vol)
+    status = "ok"
+    try:
+        st = B.jtrlan_solve(ctx)
+    except B.JTRLanError as e:
+        if e.status != B.JTRLAN_ENOCONV:
+            raise
+        status, st = "stopped at max_restarts", {}
+    torch.cuda.synchronize()
+    out = {"workload": args.one_step, "seconds": time.perf_counter() - t0, "status": status, "degree": len(g) - 1,
+           "gs_split": bool(args.gs_split), "max_restarts": args.max_restarts,
+           **{k: st.get(k) for k in ("n_matvec", "n_restarts", "n_gs_passes", "n_launches")}}
+    B.jtrlan_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1230,9 +1294,15 @@ def main():
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-restarts", type=int, default=4, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-primitives", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--one-step", default=None, help="one learned-filter step on this workload (for profilers)")
+    ap.add_argument("--gs-split", action="store_true", help="with --one-step: separate-launch Gram-Schmidt")
+    ap.add_argument("--max-restarts", type=int, default=0, help="with --one-step: bound on outer iterations")
     args = ap.parse_args()
     if args.batched_oracle_sample:
         print(json.dumps({"seconds": batched_oracle_sample([int(i) for i in args.batched_oracle_sample.split(",")])}))
+        return
+    if args.one_step:
+        one_step(args)
         return
     if args.oracle_primitives:
         print(json.dumps(oracle_primitives(args.oracle_primitives)))
@@ -1273,7 +1343,8 @@ def main():
         from paper_2001_07428_gb300 import binding as B
         B.load()
         shape = tuple(int(v) for v in args.batch_shape.split(",")) if args.batch_shape else None
-        print(json.dumps(batched_dense(B, torch, torch.cuda.current_stream(), args.steps, args.warmup,
+        peaks = B.jtrlan_measure_peaks(torch.cuda.current_stream().cuda_stream)
+        print(json.dumps(batched_dense(B, torch, torch.cuda.current_stream(), args.steps, args.warmup, peaks=peaks,
                                        cpu=not args.no_cpu_baseline, count=args.batch_count, shape=shape,
                                        forms=tuple(args.batch_forms.split(",")))), flush=True)
         return

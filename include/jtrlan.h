@@ -371,10 +371,21 @@ jtrlan_status jtrlan_batch_create(int count, const jtrlan_operator* ops, const j
 jtrlan_status jtrlan_batch_set_shape(jtrlan_batch* b, int threads, int ctas_per_sm);
 
 /* Autotuner: solves the batch once per candidate launch shape (128, 256, 512 threads; 1 .. the
- * occupancy limit of CTAs per SM), timing each with CUDA events, and keeps the fastest for later
- * solves.  Any output pointer may be NULL.  Leaves the results of the last candidate in place.
- * Errors: JTRLAN_EINVAL, JTRLAN_ECUDA. */
+ * occupancy limit of CTAs per SM), timing each with CUDA events, then, at the fastest shape, once per
+ * candidate tile shape (jtrlan_batch_set_tiles: 1 or 2 product rows per warp; in the compensated form
+ * also all, 1, 2 or 4 update groups), and keeps the fastest of all for later solves (read the tiles
+ * with jtrlan_batch_get_tiles).  Any output pointer may be NULL; *best_ms is the fastest time seen.
+ * Leaves the results of the last candidate in place.  Errors: JTRLAN_EINVAL, JTRLAN_ECUDA. */
 jtrlan_status jtrlan_batch_tune(jtrlan_batch* b, int* threads, int* ctas_per_sm, double* best_ms);
+
+/* Tile shapes of the persistent kernel.  mv_rows: rows of the product A v that a warp takes at once
+ * (1 or 2; two rows share the loads of v).  gs_groups (compensated form only): the most thread groups
+ * that split the columns of the Gram-Schmidt update y -= V c_v + W c_w, each group walking the row
+ * pairs of the instance (0: as many as the block holds; fewer groups give longer column walks and a
+ * shorter cross-group sum).  Results agree up to summation order.  Defaults: mv_rows 2 (compensated)
+ * or 1 (FP64), gs_groups 0.  Errors: JTRLAN_EINVAL (values out of range). */
+jtrlan_status jtrlan_batch_set_tiles(jtrlan_batch* b, int mv_rows, int gs_groups);
+jtrlan_status jtrlan_batch_get_tiles(jtrlan_batch* b, int* mv_rows, int* gs_groups);
 
 /* Solves every instance in one persistent launch (captured once into a CUDA graph per launch shape,
  * replayed afterwards) and waits for it.  stats may be NULL.  Returns JTRLAN_OK if all instances
@@ -437,6 +448,14 @@ jtrlan_status jtrlan_mlp_train(jtrlan_mlp* net, const float* X, const float* T, 
                                float* loss_hist);
 
 void jtrlan_mlp_destroy(jtrlan_mlp* net);
+
+/* Measured arithmetic peaks of the current device, the denominators of roofline fractions (the
+ * paper has no counterpart): best of five timed launches of throughput loops that fill every SM with
+ * independent accumulator chains -- FP64 FMA on the CUDA cores, FP64 mma.sync m8n8k4 (the FP64 tensor
+ * path), FP32 FMA -- in TFLOP/s (an FMA counts 2 flop).  Any output may be NULL.  Takes about 0.5 s;
+ * allocates and frees a small scratch buffer; synchronises cuda_stream.  Errors: JTRLAN_ECUDA. */
+jtrlan_status jtrlan_measure_peaks(double* fp64_fma_tflops, double* fp64_mma_tflops, double* fp32_fma_tflops,
+                                   void* cuda_stream);
 
 /* Static text for a status code. */
 const char* jtrlan_status_string(jtrlan_status s);

@@ -26,7 +26,8 @@ EXPORTED = ["jtrlan_create", "jtrlan_apply", "jtrlan_solve", "jtrlan_pairs", "jt
             "jtrlan_batch_results", "jtrlan_batch_vectors", "jtrlan_batch_destroy", "jtrlan_apply_filter", "jtrlan_bounds",
             "jtrlan_damped_step", "jtrlan_mlp_param_count", "jtrlan_mlp_create", "jtrlan_mlp_get_params",
             "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train",
-            "jtrlan_mlp_destroy", "jtrlan_rotate_df", "jtrlan_set_filter"]
+            "jtrlan_mlp_destroy", "jtrlan_rotate_df", "jtrlan_set_filter", "jtrlan_measure_peaks",
+            "jtrlan_batch_set_tiles", "jtrlan_batch_get_tiles"]
 NOALLOC_MAX_PARTIALS = 262144   # JTRLAN_NOALLOC_MAX_PARTIALS
 NOALLOC_MAX_COLS = 1024         # JTRLAN_NOALLOC_MAX_COLS
 
@@ -132,12 +133,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jtrlan_batch_set_shape.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     lib.jtrlan_batch_tune.argtypes = [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double)]
     lib.jtrlan_batch_solve.argtypes = [ctypes.c_void_p, P(jtrlan_batch_stats)]
+    lib.jtrlan_batch_set_tiles.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    lib.jtrlan_batch_get_tiles.argtypes = [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int)]
     lib.jtrlan_batch_results.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.jtrlan_batch_vectors.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     lib.jtrlan_batch_destroy.argtypes = [ctypes.c_void_p]
     lib.jtrlan_batch_destroy.restype = None
     lib.jtrlan_apply_filter.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.jtrlan_bounds.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)]
+    lib.jtrlan_measure_peaks.argtypes = [P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), ctypes.c_void_p]
     lib.jtrlan_set_filter.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
     lib.jtrlan_damped_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.jtrlan_mlp_param_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -160,7 +164,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
               "jtrlan_batch_tune", "jtrlan_batch_solve", "jtrlan_batch_results", "jtrlan_batch_vectors",
               "jtrlan_apply_filter", "jtrlan_bounds", "jtrlan_damped_step", "jtrlan_mlp_create", "jtrlan_mlp_get_params",
               "jtrlan_mlp_set_params", "jtrlan_mlp_forward", "jtrlan_mlp_gradient", "jtrlan_mlp_train",
-              "jtrlan_rotate_df", "jtrlan_set_filter"):
+              "jtrlan_rotate_df", "jtrlan_set_filter", "jtrlan_measure_peaks", "jtrlan_batch_set_tiles",
+              "jtrlan_batch_get_tiles"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -230,7 +235,17 @@ def jtrlan_batch_set_shape(b, threads: int, ctas_per_sm: int):
 def jtrlan_batch_tune(b) -> dict:
     t, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(load().jtrlan_batch_tune(b, ctypes.byref(t), ctypes.byref(c), ctypes.byref(ms)))
-    return dict(threads=t.value, ctas_per_sm=c.value, best_ms=ms.value)
+    return dict(threads=t.value, ctas_per_sm=c.value, best_ms=ms.value, **jtrlan_batch_get_tiles(b))
+
+
+def jtrlan_batch_set_tiles(b, mv_rows: int, gs_groups: int):
+    _check(load().jtrlan_batch_set_tiles(b, int(mv_rows), int(gs_groups)))
+
+
+def jtrlan_batch_get_tiles(b) -> dict:
+    r, g = ctypes.c_int(), ctypes.c_int()
+    _check(load().jtrlan_batch_get_tiles(b, ctypes.byref(r), ctypes.byref(g)))
+    return dict(mv_rows=r.value, gs_groups=g.value)
 
 
 def jtrlan_batch_solve(b, check: bool = True) -> dict:
@@ -265,6 +280,13 @@ def jtrlan_bounds(ctx, steps: int):
     lo, hi = ctypes.c_double(), ctypes.c_double()
     _check(load().jtrlan_bounds(ctx, int(steps), ctypes.byref(lo), ctypes.byref(hi)))
     return lo.value, hi.value
+
+
+def jtrlan_measure_peaks(stream: int = 0) -> dict:
+    """Measured FP64 FMA, FP64 tensor (mma.sync m8n8k4) and FP32 FMA throughput of the device, TFLOP/s."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().jtrlan_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.c_void_p(stream)))
+    return {"fp64_fma_tflops": a.value, "fp64_mma_tflops": b.value, "fp32_fma_tflops": c.value}
 
 
 def jtrlan_set_filter(ctx, coeffs, window):

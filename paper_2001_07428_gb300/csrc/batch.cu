@@ -226,12 +226,106 @@ __device__ void cta_matvec_df(const float4* A11, const float4* A12, int64_t h, c
 
 // y = A x (dense block form); x and y in shared memory (FP64), A rows from global.  Returns the
 // block-wide Re/Im of x^H y in (*ar, *ai) when requested.
+// The same with one row per warp at a time (the tile shape the autotuner may pick for small orders):
+// four sums, one reduce-scatter per row.
+__device__ void cta_matvec_df1(const float4* A11, const float4* A12, int64_t h, const float4* x4, double2* y) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int C = (int)((h + 31) >> 5);
+  const int R = (w < h) ? (int)((h - 1 - w) / nw) + 1 : 0;
+  const int total = R * C;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto fetch = [&](int q, int u, float4& a0, float4& b0) {
+    const int64_t c = lane + 32 * u;
+    const int64_t r0 = w + (int64_t)q * nw;
+    a0 = b0 = z4;
+    if (c < h) {
+      a0 = A11[r0 * h + c];
+      b0 = A12[r0 * h + c];
+    }
+  };
+  float4 ca0, cb0;
+  if (total > 0) fetch(0, 0, ca0, cb0);
+  float s[4], e[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] = e[k] = 0.f;
+  int q = 0, u = 0;
+  for (int it = 0; it < total; ++it) {
+    int qn = q, un = u + 1;
+    if (un == C) {
+      un = 0;
+      ++qn;
+    }
+    float4 na0 = z4, nb0 = z4;
+    if (it + 1 < total) fetch(qn, un, na0, nb0);
+    const int64_t c = lane + 32 * u;
+    if (c < h) {
+      const float4 x1 = x4[c], x2 = x4[h + c];
+      b_cacc(&s[0], &e[0], ca0, x1);          // y1 = A11 x1 + A12 x2
+      b_cacc(&s[0], &e[0], cb0, x2);
+      b_caccc(&s[2], &e[2], ca0, x2);         // y2 = conj(A11) x2 - conj(A12) x1
+      b_caccc(&s[2], &e[2], cb0, x1, -1.f);
+    }
+    if (u == C - 1) {
+      const double v = df_reduce4(s, e);      // lane L holds sum (L >> 3) & 3
+      const int64_t row = w + (int64_t)q * nw;
+      if ((lane & 7) == 0) {
+        const int comp = lane >> 3;           // y1.re, y1.im, y2.re, y2.im
+        ((double*)y)[comp < 2 ? 2 * row + comp : 2 * (h + row) + comp - 2] = v;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s[k] = e[k] = 0.f;
+    }
+    ca0 = na0;
+    cb0 = nb0;
+    q = qn;
+    u = un;
+  }
+}
+
 template <bool DF>
 __device__ void cta_matvec(const BatchArgs& a, int64_t h, int64_t off, const double2* x, const float4* x4, double2* y,
                            double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if constexpr (DF) {
-    cta_matvec_df((const float4*)a.A11 + off, (const float4*)a.A12 + off, h, x4, y);
+    if (a.mv_rows == 1)
+      cta_matvec_df1((const float4*)a.A11 + off, (const float4*)a.A12 + off, h, x4, y);
+    else
+      cta_matvec_df((const float4*)a.A11 + off, (const float4*)a.A12 + off, h, x4, y);
+  } else if (a.mv_rows == 2) {   // two rows per warp (r and r + nw) sharing the loads of x
+    for (int64_t r = w; r < h; r += 2 * nw) {
+      const int64_t r2 = r + nw;
+      const bool two = r2 < h;
+      const double2* r11 = (const double2*)a.A11 + off + r * h;
+      const double2* r12 = (const double2*)a.A12 + off + r * h;
+      const double2* s11 = (const double2*)a.A11 + off + (two ? r2 : r) * h;
+      const double2* s12 = (const double2*)a.A12 + off + (two ? r2 : r) * h;
+      double2 y1 = make_double2(0, 0), y2 = make_double2(0, 0), z1 = make_double2(0, 0), z2 = make_double2(0, 0);
+      for (int64_t c = lane; c < h; c += 32) {
+        const double2 x1 = x[c], x2 = x[h + c];
+        const double2 a11 = r11[c], a12 = r12[c];
+        y1 = cfma(a11, x1, y1);
+        y1 = cfma(a12, x2, y1);
+        y2 = cfmac(a11, x2, y2);
+        y2 = cfmac(make_double2(-a12.x, -a12.y), x1, y2);
+        if (two) {
+          const double2 b11 = s11[c], b12 = s12[c];
+          z1 = cfma(b11, x1, z1);
+          z1 = cfma(b12, x2, z1);
+          z2 = cfmac(b11, x2, z2);
+          z2 = cfmac(make_double2(-b12.x, -b12.y), x1, z2);
+        }
+      }
+      const double v0 = warp_sum(y1.x), v1 = warp_sum(y1.y), v2 = warp_sum(y2.x), v3 = warp_sum(y2.y);
+      const double u0 = warp_sum(z1.x), u1 = warp_sum(z1.y), u2 = warp_sum(z2.x), u3 = warp_sum(z2.y);
+      if (lane == 0) {
+        y[r] = make_double2(v0, v1);
+        y[h + r] = make_double2(v2, v3);
+        if (two) {
+          y[r2] = make_double2(u0, u1);
+          y[h + r2] = make_double2(u2, u3);
+        }
+      }
+    }
   } else {
     for (int64_t r = w; r < h; r += nw) {
       const double2* r11 = (const double2*)a.A11 + off + r * h;
@@ -347,7 +441,7 @@ __device__ void cta_dot(const void* Vv, int64_t n, int64_t h, int j, const doubl
 // (8 floats per thread) and group 0 adds them and updates y.
 template <bool DF>
 __device__ double cta_update(const void* Vv, int64_t n, int64_t h, int j, const double* coef, const float4* coef4,
-                             double2* y, float* part, double* red) {
+                             double2* y, float* part, double* red, int gs_groups) {
   double nrm = 0.0;
   if constexpr (DF) {
     const float4* V = (const float4*)Vv;
@@ -385,7 +479,8 @@ __device__ double cta_update(const void* Vv, int64_t n, int64_t h, int j, const 
     const int hp = (int)(((h + 31) >> 5) << 5);
     float s[4], e[4];
     if (hp <= (int)blockDim.x) {               // one sweep: G groups of hp threads
-      const int G = (int)blockDim.x / hp;
+      int G = (int)blockDim.x / hp;
+      if (gs_groups > 0 && G > gs_groups) G = gs_groups;   // tile shape: fewer, longer column walks
       const int g = (int)threadIdx.x / hp, tl = (int)threadIdx.x - g * hp;
       const bool active = g < G && tl < h;
       if (active) accumulate(tl, g, G, s, e);
@@ -882,7 +977,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(BatchArgs a) {
         mark(0);
         for (int pass = 0; pass < a.gs_passes; ++pass) {         // against W_j and V_j, sqrt(2) test
           cta_dot<DF>(V, n, h, j, y, x4, S.coef, S.coef4);
-          b1 = sqrt(cta_update<DF>(V, n, h, j, S.coef, S.coef4, y, part, S.red));
+          b1 = sqrt(cta_update<DF>(V, n, h, j, S.coef, S.coef4, y, part, S.red, a.gs_groups));
           ++n_gs;
           if (sqrt2 * b1 > b0) break;
           b0 = b1;

@@ -64,6 +64,9 @@ struct jtrlan_batch {
   int ctas_per_sm = 0;          // 0: as many as fit
   cudaGraphExec_t exec = nullptr;
   int exec_grid = 0, exec_threads = 0;
+  int mv_rows = 0;              // tile shape (0 until set: the form's default, see tiles_of)
+  int gs_groups = 0;            // 0: as many update groups as fit
+  int exec_mv_rows = -1, exec_gs_groups = -1;
   bool solved = false;
   std::vector<void*> allocs;
 
@@ -264,6 +267,10 @@ BatchArgs args_of(const jtrlan_batch* b) {
   a.vec_off = b->d_voff;
   a.prof = b->prof;
   a.queue = b->queue;
+  // default tile: two product rows per warp in the compensated form, one in FP64 (measured best
+  // before the tile search existed); the autotuner may change both
+  a.mv_rows = b->mv_rows > 0 ? b->mv_rows : (b->df ? 2 : 1);
+  a.gs_groups = b->gs_groups;
   return a;
 }
 
@@ -272,7 +279,8 @@ jtrlan_status run_once(jtrlan_batch* b, int threads, int ctas_per_sm, bool graph
   int grid = 0;
   JB_TRY(shape(b, threads, ctas_per_sm, &grid));
   const BatchArgs a = args_of(b);
-  if (graph && (!b->exec || b->exec_grid != grid || b->exec_threads != threads)) {
+  if (graph && (!b->exec || b->exec_grid != grid || b->exec_threads != threads || b->exec_mv_rows != a.mv_rows ||
+                b->exec_gs_groups != a.gs_groups)) {
     if (b->exec) {
       JB_CUDA(cudaGraphExecDestroy(b->exec));
       b->exec = nullptr;
@@ -290,6 +298,8 @@ jtrlan_status run_once(jtrlan_batch* b, int threads, int ctas_per_sm, bool graph
     JB_CUDA(e4);
     b->exec_grid = grid;
     b->exec_threads = threads;
+    b->exec_mv_rows = a.mv_rows;
+    b->exec_gs_groups = a.gs_groups;
   }
   JB_CUDA(cudaEventRecord(b->ej, b->user));
   JB_CUDA(cudaStreamWaitEvent(b->own, b->ej, 0));
@@ -361,10 +371,48 @@ jtrlan_status jtrlan_batch_tune(jtrlan_batch* b, int* threads_out, int* ctas_per
   }
   b->threads = best_t;
   b->ctas_per_sm = best_c;
+  // tile shapes at the chosen launch shape: rows of the product per warp, and (compensated form) the
+  // number of thread groups that split the columns of the Gram-Schmidt update
+  const int cand_rows[] = {1, 2};
+  const int cand_groups_df[] = {0, 1, 2, 4};
+  const int cand_groups_64[] = {0};
+  const int* groups = b->df ? cand_groups_df : cand_groups_64;
+  const int ngroups = b->df ? 4 : 1;
+  int best_r = b->df ? 2 : 1, best_g = 0;
+  for (int r : cand_rows)
+    for (int q = 0; q < ngroups; ++q) {
+      b->mv_rows = r;
+      b->gs_groups = groups[q];
+      JB_TRY(run_once(b, best_t, best_c, false, &ms));
+      if (ms < best) {
+        best = ms;
+        best_r = r;
+        best_g = groups[q];
+      }
+    }
+  b->mv_rows = best_r;
+  b->gs_groups = best_g;
   if (threads_out) *threads_out = best_t;
   if (ctas_per_sm_out) *ctas_per_sm_out = best_c;
   if (best_ms) *best_ms = best;
   b->solved = true;
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_batch_set_tiles(jtrlan_batch* b, int mv_rows, int gs_groups) {
+  if (!b) return bfail(JTRLAN_EINVAL, "null batch");
+  if (mv_rows != 1 && mv_rows != 2) return bfail(JTRLAN_EINVAL, "mv_rows must be 1 or 2");
+  if (gs_groups < 0 || gs_groups > 16) return bfail(JTRLAN_EINVAL, "gs_groups must be 0..16");
+  b->mv_rows = mv_rows;
+  b->gs_groups = gs_groups;
+  return JTRLAN_OK;
+}
+
+jtrlan_status jtrlan_batch_get_tiles(jtrlan_batch* b, int* mv_rows, int* gs_groups) {
+  if (!b) return bfail(JTRLAN_EINVAL, "null batch");
+  const BatchArgs a = args_of(b);
+  if (mv_rows) *mv_rows = a.mv_rows;
+  if (gs_groups) *gs_groups = a.gs_groups;
   return JTRLAN_OK;
 }
 

@@ -215,6 +215,8 @@ struct BatchArgs {
   const int64_t* vec_off;
   long long* prof;
   int* queue;
+  int mv_rows;     // tile: rows of the product a warp takes at once (1 or 2; they share the loads of x)
+  int gs_groups;   // tile: most thread groups splitting the columns of the compensated update (0: all that fit)
 };
 constexpr int kBatchStats = 6;
 constexpr int kBatchPhases = 5;   // Lanczos product + alpha, Gram-Schmidt, Ritz, rotation + shrink, residuals

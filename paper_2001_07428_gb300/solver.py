@@ -140,6 +140,9 @@ class JTRLanBatch:
     def set_shape(self, threads, ctas_per_sm=0):
         B.jtrlan_batch_set_shape(self.b, threads, ctas_per_sm)
 
+    def set_tiles(self, mv_rows, gs_groups=0):
+        B.jtrlan_batch_set_tiles(self.b, mv_rows, gs_groups)
+
     def solve(self, check=True) -> dict:
         return B.jtrlan_batch_solve(self.b, check=check)
 

@@ -1,13 +1,18 @@
 """Train the filter network on plain runs of the method (GPU).
 
-    python -m paper_2001_07428_gb300.train_filter [--runs 96,24,8] [--steps 6000] [--data PATH] [--out PATH]
+    python -m paper_2001_07428_gb300.train_filter [--runs 1000,1000,8] [--steps 6000] [--data PATH] [--out PATH]
+                                                  [--generate] [--concurrency P] [--tol 1e-7]
 
 With --data naming an existing file (default: the committed filter_runs.json) the plain runs are read
-from it instead of being generated again.
+from it; --generate runs them again and writes that file.
 
-1. Seeded plain runs (JTRLAN_MIXED_REORTH, no filter, residual 1e-7) on 8^4, 12^4 and 16^4 lattices
-   with m0 ~ U[8, 10], kappa ~ U[0.1, 0.5], links from inputs.stencil_links: the lowest 101
-   eigenvalues of each, and the spectral window from jtrlan_bounds (the network's inputs).
+1. Seeded plain runs (JTRLAN_MIXED_REORTH, no filter) on 8^4 and 12^4 lattices (and a few 16^4 runs
+   that cover the smallest nev/sites fractions) with m0 ~ U[8, 10], kappa ~ U[0.1, 0.5], links from
+   inputs.stencil_links, run i seeded with 1000 + i: the lowest 101 eigenvalues of each, and the
+   spectral window from jtrlan_bounds (the network's inputs).  With --concurrency P, P runs proceed at
+   once, each on its own CUDA stream and context (small lattices leave most of the GPU idle); these
+   runs use the separate-launch Gram-Schmidt and the CUDA-core rotation, so that no cooperative or
+   tensor-memory kernel of one run waits for resources another run holds.
 2. Samples: for each run and each nev in NEV_GRID, features -> Jackson-damped step coefficients with
    the cut between lambda_nev and lambda_{nev+1} (the library's jtrlan_damped_step kernel).
 3. Full-batch Adam in the library's kernels (jtrlan_mlp_train); every 8th run is held out.
@@ -20,9 +25,12 @@ import json
 import os
 import time
 
+import ctypes
+
 import numpy as np
 import torch
 
+from . import binding as B
 from . import inputs
 from . import learned_filter as LF
 from .solver import JTRLan
@@ -31,19 +39,51 @@ LATTICES = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16)]
 NEV_TRUTH = 101
 
 
-def run_record(i, dims, device="cuda"):
+def run_record(i, dims, device="cuda", tol=1e-7, isolated=False):
     """One plain run: (m0, kappa, sites, lo, hi, the lowest NEV_TRUTH eigenvalues)."""
     rng = np.random.default_rng(1000 + i)
     m0 = float(rng.uniform(8.0, 10.0))
     kappa = float(rng.uniform(0.1, 0.5))
     U, W = inputs.stencil_links(dims, 1000 + i)
+    t0 = time.perf_counter()
     lo, hi = LF.stencil_bounds(U, W, dims, m0, kappa, device)
     s = JTRLan(kind="stencil", dims=dims, m0=m0, kappa=kappa, U=U, W=W, nev=NEV_TRUTH, m=220, mwin=100,
-               tol=1e-7, precision="mixed_reorth", device=device)
-    s.solve()
-    ev, _, _ = s.pairs()
+               tol=tol, precision="mixed_reorth", gs_split=isolated, rotate_simt=isolated, device=device)
+    st = s.solve()
+    ev = np.zeros(NEV_TRUTH)
+    B.jtrlan_pairs(s.ctx, 0, ev.ctypes.data_as(ctypes.c_void_p), None, None)
     s.close()
-    return dict(i=i, dims=list(dims), m0=m0, kappa=kappa, sites=int(np.prod(dims)), lo=lo, hi=hi, ev=ev.tolist())
+    return dict(i=i, dims=list(dims), m0=m0, kappa=kappa, sites=int(np.prod(dims)), lo=lo, hi=hi, ev=ev.tolist(),
+                tol=tol, n_matvec=int(st["n_matvec"]), seconds=round(time.perf_counter() - t0, 3))
+
+
+def generate(plan, device="cuda", tol=1e-7, concurrency=1, log=None):
+    """Runs the plain runs of `plan` (a list of (i, dims)); with concurrency > 1, that many at once,
+    each in a host thread with its own CUDA stream (the library releases the interpreter lock in its
+    calls, and each context enqueues on the stream current at its creation)."""
+    if concurrency <= 1:
+        out = []
+        for i, dims in plan:
+            out.append(run_record(i, dims, device, tol))
+            if log:
+                log(out[-1])
+        return out
+    import concurrent.futures as cf
+    import threading
+    local = threading.local()
+
+    def work(item):
+        i, dims = item
+        if not hasattr(local, "stream"):
+            local.stream = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(local.stream):
+            r = run_record(i, dims, device, tol, isolated=True)
+        if log:
+            log(r)
+        return r
+
+    with cf.ThreadPoolExecutor(max_workers=concurrency) as ex:
+        return sorted(ex.map(work, plan), key=lambda r: r["i"])
 
 
 def samples(records, device="cuda"):
@@ -65,25 +105,29 @@ def tau_of(coeffs):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--runs", default="96,24,8", help="runs per lattice (8^4, 12^4, 16^4)")
+    ap.add_argument("--runs", default="1000,1000,8", help="runs per lattice (8^4, 12^4, 16^4)")
     ap.add_argument("--steps", type=int, default=6000)
-    ap.add_argument("--data", default=LF.RUNS, help="cached plain-run records (json); generated if missing")
+    ap.add_argument("--data", default=LF.RUNS, help="plain-run records (json)")
+    ap.add_argument("--generate", action="store_true", help="run the plain runs again and write --data")
+    ap.add_argument("--concurrency", type=int, default=1)
+    ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--out", default=LF.WEIGHTS)
     args = ap.parse_args()
     counts = [int(c) for c in args.runs.split(",")]
     t0 = time.perf_counter()
-    records = []
-    if args.data and os.path.exists(args.data):
-        records = json.load(open(args.data))
-    else:
-        i = 0
+    if args.generate or not os.path.exists(args.data):
+        plan, i = [], 0
         for dims, cnt in zip(LATTICES, counts):
-            for _ in range(cnt):
-                records.append(run_record(i, dims))
-                i += 1
-        if args.data:
-            json.dump(records, open(args.data, "w"))
+            plan += [(i + k, dims) for k in range(cnt)]
+            i += cnt
+        records = generate(plan, tol=args.tol, concurrency=args.concurrency,
+                           log=lambda r: print(json.dumps({k: r[k] for k in ("i", "dims", "seconds", "n_matvec")}),
+                                               flush=True))
+        json.dump(records, open(args.data, "w"))
+    else:
+        records = json.load(open(args.data))
     t_data = time.perf_counter() - t0
+    counts = [sum(1 for r in records if tuple(r["dims"]) == tuple(d)) for d in LATTICES]
     X, T, taus, groups = samples(records)
     val = np.array([r["i"] % 8 == 7 for r in records])
     val_ids = {r["i"] for r, v in zip(records, val) if v}

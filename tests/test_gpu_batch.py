@@ -183,3 +183,31 @@ def test_plain_trlan_matches_oracle_on_case_a(precision):
     st_js = js.solve()
     js.close()
     assert st["n_matvec"] > 1.5 * st_js["n_matvec"] and abs(st["n_matvec"] - ref["n_matvec"]) <= 0.2 * ref["n_matvec"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_reorth"])
+def test_batch_tile_shapes_agree_with_the_oracle(precision):
+    """Every tile shape the autotuner searches (1 or 2 product rows per warp; all, 1, 2 or 4 update
+    groups) returns the oracle's eigenvalues; the tuner's choice is readable afterwards."""
+    sizes = inputs.batched_dense_sizes(12, 64, 300, seed=13)
+    blocks = _instances(sizes, 900)
+    nev, m, mwin, tol = 8, 24, 12, 1e-10
+    ref = [tj.trlan_jsym(lambda x, a=a, b=b: jsym.dense_matvec(a, b, x), int(n), nev, m, mwin, 1e-12)["evals"]
+           for (a, b), n in zip(blocks, sizes)]
+    ref = np.array(ref)
+    b = _batch(blocks, nev=nev, m=m, mwin=mwin, tol=tol, precision=precision)
+    groups = (0, 1, 2, 4) if precision == "mixed_reorth" else (0,)
+    for rows in (1, 2):
+        for g in groups:
+            b.set_tiles(rows, g)
+            b.solve()
+            ev, res, ist = b.results()
+            assert (ist[:, 2] == 0).all() and (res < tol).all()
+            assert (np.abs(ev - ref) / np.abs(ref)).max() < 1e-10, (rows, g)
+    from paper_2001_07428_gb300 import binding as B
+    tuned = B.jtrlan_batch_tune(b.b)
+    assert tuned["mv_rows"] in (1, 2) and tuned["gs_groups"] in groups
+    b.solve()
+    ev, _, _ = b.results()
+    assert (np.abs(ev - ref) / np.abs(ref)).max() < 1e-10
+    b.close()
