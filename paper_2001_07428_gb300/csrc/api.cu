@@ -749,11 +749,11 @@ jtrlan_status lanczos_steps(jtrlan_ctx* c, Phase& ph, GSArgs& a, int j0, int j1,
       }
       LAUNCH(K_GS_FIRST, launch_gsdf_first(a, ph.x, (const double2*)ph.alpha_part, mv_parts, s));
       LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 1, s));
-      LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
+      LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, 1, s));
       for (int pass = 2; pass <= c->gs_passes; ++pass) {
         LAUNCH(K_GS_DOT, launch_gsdf_dot(a, pass, s));
         LAUNCH(K_GS_REDUCE, launch_gs_reduce(a, 0, s));
-        LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, s));
+        LAUNCH(K_GS_UPDATE, launch_gsdf_update(a, pass, s));
       }
       LAUNCH(K_GS_NORMALIZE, launch_gsdf_normalize(a, ph.x, s));
     } else {

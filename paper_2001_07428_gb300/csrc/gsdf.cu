@@ -48,6 +48,16 @@ __device__ __forceinline__ void df_acc(float& s, float& e, float ah, float al, f
 __device__ __forceinline__ void df_sub(float& s, float& e, float ah, float al, float bh, float bl) {
   df_acc(s, e, -ah, -al, bh, bl);
 }
+// (s, e) += a * (bh + bl) for an a that is exact in FP32 (a complex64 link): the exact split of
+// a * bh into the sum, a * bl and the rounding errors into e -- 11 FP32 operations.
+__device__ __forceinline__ void df_acc_xa(float& s, float& e, float a, float bh, float bl) {
+  const float p = __fmul_rn(a, bh);
+  const float pe = __fmaf_rn(a, bh, -p);
+  float t, te;
+  two_sum(s, p, t, te);
+  s = t;
+  e = __fmaf_rn(a, bl, __fadd_rn(e, __fadd_rn(te, pe)));
+}
 
 __device__ __forceinline__ float4 split(double2 v) {
   const float hx = (float)v.x, hy = (float)v.y;
@@ -259,50 +269,90 @@ __global__ void __launch_bounds__(kThreads, kDotMinBlocks) gsdf_dot_kernel(GSArg
   dfdot_body(a, p0, p1, ys, red, blockIdx.x);
 }
 
-// y -= V c_v + W c_w over rows [p0, p1): warp q owns rows p0 + 32 q + lane, then + 256, ...; every
-// column is accumulated per row in compensated FP32 (four columns' loads in flight), converted once
-// and applied to y in FP64 by the warp that owns the row: no cross-warp reduction and no barrier.
-// Returns this thread's share of ||y||^2.  The branch depends only on the block's row range, so it is
-// uniform across the block (dfupdate_split has barriers).
-// Blocks with fewer than 256 rows (the small lattices' cooperative partition) take dfupdate_split
-// instead, so that no warp idles.
+// The update's coefficients in shared memory, classified once per launch (every block alike):
+// column i is "large" when some component of c_v or c_w exceeds thr = 2^-27 ||y|| / ((j+1)(j+4)).
+// Large columns are applied in compensated FP32 from their (hi, lo) splits scf[2i], scf[2i+1]; the
+// others enter one plain FP32 sum through csm[i] = (c_v.re, c_v.im, c_w.re, c_w.im) rounded to FP32
+// (zero for a large column), with the hi parts of V.  Each term of that sum is off by at most
+// (j + 4) 2^-24 of |v c| (product, the dropped lo parts, the recursive sum), so the whole plain part
+// errs by at most (j+4) 2^-24 sum_i |c_i| <= 2^-51 ||y||: below the compensated arithmetic's own error.
+// In a Lanczos step nearly every coefficient is of rounding size (exactly, only beta_{j-1} and, after
+// a restart, the arrow couplings are not), so the update costs about one read of V instead of 16
+// compensated products per row pair and column.
+struct UpdCoef {
+  float4* scf;          // [2 (m+1)] (hi, lo) splits of c_v, c_w
+  float4* csm;          // [m+1] FP32 coefficients of the plain sum (zero for large columns)
+  unsigned char* big;   // [m+1] 1 for a large column
+};
+
+__device__ __forceinline__ void classify_coefs(const coef4* coef, int j, double ynorm, UpdCoef u) {
+  const double thr = ldexp(ynorm, -27) / ((double)(j + 1) * (double)(j + 4));
+  for (int i = threadIdx.x; i <= j; i += kThreads) {
+    const coef4 c = coef[i];
+    u.scf[2 * i] = split(make_double2(c.vr, c.vi));
+    u.scf[2 * i + 1] = split(make_double2(c.wr, c.wi));
+    const bool large = fmax(fmax(fabs(c.vr), fabs(c.vi)), fmax(fabs(c.wr), fabs(c.wi))) > thr;
+    u.big[i] = large ? 1 : 0;
+    u.csm[i] = large ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4((float)c.vr, (float)c.vi, (float)c.wr, (float)c.wi);
+  }
+}
+
+// y -= V c_v + W c_w over rows [p0, p1): warp q owns rows p0 + 32 q + lane, then + 256, ...; the
+// small columns go into a plain FP32 sum (four columns' loads in flight), the large ones into a
+// compensated one; both are converted once and applied to y in FP64 by the warp that owns the row:
+// no cross-warp reduction and no barrier.  Returns this thread's share of ||y||^2.  The branch
+// depends only on the block's row range, so it is uniform across the block (dfupdate_split has
+// barriers).  Blocks with fewer than 256 rows (the small lattices' cooperative partition) take
+// dfupdate_split instead, so that no warp idles; it applies every column in compensated FP32.
 __device__ double dfupdate_split(const GSArgs& a, int64_t p0, int64_t p1, const float4* scf, float (*red_s)[32][4],
                                  float (*red_e)[32][4]);
-__device__ double dfupdate_rows(const GSArgs& a, int64_t p0, int64_t p1, const float4* scf, float (*red_s)[32][4],
+__device__ double dfupdate_rows(const GSArgs& a, int64_t p0, int64_t p1, UpdCoef u, float (*red_s)[32][4],
                                 float (*red_e)[32][4]) {
-  if (p1 - p0 < 32 * kGroups) return dfupdate_split(a, p0, p1, scf, red_s, red_e);
+  if (p1 - p0 < 32 * kGroups) return dfupdate_split(a, p0, p1, u.scf, red_s, red_e);
   const float4* V = (const float4*)a.V;
   double2* y = (double2*)a.y;
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   const int64_t n = a.n, h = a.h;
   const int j = a.j;
+  const float4* scf = u.scf;
   double nrm = 0.0;
   for (int64_t p = p0 + 32 * q + lane; p < p1; p += 32 * kGroups) {
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f}, sp[4] = {0.f, 0.f, 0.f, 0.f};
     int i = 0;
     for (; i + 3 <= j; i += 4) {
       float4 v1u[4], v2u[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        v1u[u] = V[(int64_t)(i + u) * n + p];
-        v2u[u] = V[(int64_t)(i + u) * n + h + p];
+      for (int t = 0; t < 4; ++t) {
+        v1u[t] = V[(int64_t)(i + t) * n + p];
+        v2u[t] = V[(int64_t)(i + t) * n + h + p];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4 v1 = v1u[u], v2 = v2u[u];
-        const float4 cv = scf[2 * (i + u)], cw = scf[2 * (i + u) + 1];
+      for (int t = 0; t < 4; ++t) {
+        const float4 v1 = v1u[t], v2 = v2u[t], c = u.csm[i + t];   // c = (cv.re, cv.im, cw.re, cw.im)
         // y1 correction: v1 c_v - conj(v2) c_w;  y2 correction: v2 c_v + conj(v1) c_w
-        df_acc(s[0], e[0], v1.x, v1.z, cv.x, cv.z);  df_sub(s[0], e[0], v1.y, v1.w, cv.y, cv.w);
-        df_sub(s[0], e[0], v2.x, v2.z, cw.x, cw.z);  df_sub(s[0], e[0], v2.y, v2.w, cw.y, cw.w);
-        df_acc(s[1], e[1], v1.x, v1.z, cv.y, cv.w);  df_acc(s[1], e[1], v1.y, v1.w, cv.x, cv.z);
-        df_sub(s[1], e[1], v2.x, v2.z, cw.y, cw.w);  df_acc(s[1], e[1], v2.y, v2.w, cw.x, cw.z);
-        df_acc(s[2], e[2], v2.x, v2.z, cv.x, cv.z);  df_sub(s[2], e[2], v2.y, v2.w, cv.y, cv.w);
-        df_acc(s[2], e[2], v1.x, v1.z, cw.x, cw.z);  df_acc(s[2], e[2], v1.y, v1.w, cw.y, cw.w);
-        df_acc(s[3], e[3], v2.x, v2.z, cv.y, cv.w);  df_acc(s[3], e[3], v2.y, v2.w, cv.x, cv.z);
-        df_acc(s[3], e[3], v1.x, v1.z, cw.y, cw.w);  df_sub(s[3], e[3], v1.y, v1.w, cw.x, cw.z);
+        sp[0] = __fmaf_rn(v1.x, c.x, sp[0]); sp[0] = __fmaf_rn(-v1.y, c.y, sp[0]);
+        sp[0] = __fmaf_rn(-v2.x, c.z, sp[0]); sp[0] = __fmaf_rn(-v2.y, c.w, sp[0]);
+        sp[1] = __fmaf_rn(v1.x, c.y, sp[1]); sp[1] = __fmaf_rn(v1.y, c.x, sp[1]);
+        sp[1] = __fmaf_rn(-v2.x, c.w, sp[1]); sp[1] = __fmaf_rn(v2.y, c.z, sp[1]);
+        sp[2] = __fmaf_rn(v2.x, c.x, sp[2]); sp[2] = __fmaf_rn(-v2.y, c.y, sp[2]);
+        sp[2] = __fmaf_rn(v1.x, c.z, sp[2]); sp[2] = __fmaf_rn(v1.y, c.w, sp[2]);
+        sp[3] = __fmaf_rn(v2.x, c.y, sp[3]); sp[3] = __fmaf_rn(v2.y, c.x, sp[3]);
+        sp[3] = __fmaf_rn(v1.x, c.w, sp[3]); sp[3] = __fmaf_rn(-v1.y, c.z, sp[3]);
       }
     }
     for (; i <= j; ++i) {
+      const float4 v1 = V[(int64_t)i * n + p], v2 = V[(int64_t)i * n + h + p], c = u.csm[i];
+      sp[0] = __fmaf_rn(v1.x, c.x, sp[0]); sp[0] = __fmaf_rn(-v1.y, c.y, sp[0]);
+      sp[0] = __fmaf_rn(-v2.x, c.z, sp[0]); sp[0] = __fmaf_rn(-v2.y, c.w, sp[0]);
+      sp[1] = __fmaf_rn(v1.x, c.y, sp[1]); sp[1] = __fmaf_rn(v1.y, c.x, sp[1]);
+      sp[1] = __fmaf_rn(-v2.x, c.w, sp[1]); sp[1] = __fmaf_rn(v2.y, c.z, sp[1]);
+      sp[2] = __fmaf_rn(v2.x, c.x, sp[2]); sp[2] = __fmaf_rn(-v2.y, c.y, sp[2]);
+      sp[2] = __fmaf_rn(v1.x, c.z, sp[2]); sp[2] = __fmaf_rn(v1.y, c.w, sp[2]);
+      sp[3] = __fmaf_rn(v2.x, c.y, sp[3]); sp[3] = __fmaf_rn(v2.y, c.x, sp[3]);
+      sp[3] = __fmaf_rn(v1.x, c.w, sp[3]); sp[3] = __fmaf_rn(-v1.y, c.z, sp[3]);
+    }
+    for (i = 0; i <= j; ++i) {     // the large columns, compensated (uniform branch: same column for all)
+      if (!u.big[i]) continue;
       const float4 v1 = V[(int64_t)i * n + p], v2 = V[(int64_t)i * n + h + p];
       const float4 cv = scf[2 * i], cw = scf[2 * i + 1];
       df_acc(s[0], e[0], v1.x, v1.z, cv.x, cv.z);  df_sub(s[0], e[0], v1.y, v1.w, cv.y, cv.w);
@@ -315,10 +365,10 @@ __device__ double dfupdate_rows(const GSArgs& a, int64_t p0, int64_t p1, const f
       df_acc(s[3], e[3], v1.x, v1.z, cw.y, cw.w);  df_sub(s[3], e[3], v1.y, v1.w, cw.x, cw.z);
     }
     double2 y1 = y[p], y2 = y[h + p];
-    y1.x -= (double)s[0] + (double)e[0];
-    y1.y -= (double)s[1] + (double)e[1];
-    y2.x -= (double)s[2] + (double)e[2];
-    y2.y -= (double)s[3] + (double)e[3];
+    y1.x -= ((double)s[0] + (double)e[0]) + (double)sp[0];
+    y1.y -= ((double)s[1] + (double)e[1]) + (double)sp[1];
+    y2.x -= ((double)s[2] + (double)e[2]) + (double)sp[2];
+    y2.y -= ((double)s[3] + (double)e[3]) + (double)sp[3];
     y[p] = y1;
     y[h + p] = y2;
     nrm += cabs2(y1) + cabs2(y2);
@@ -386,25 +436,22 @@ __device__ double dfupdate_split(const GSArgs& a, int64_t p0, int64_t p1, const 
   return nrm;
 }
 
-__global__ void __launch_bounds__(kThreads) gsdf_update_kernel(GSArgs a) {
-  extern __shared__ float4 scf[];                       // per column: {cv hi/lo}, {cw hi/lo}
+__global__ void __launch_bounds__(kThreads) gsdf_update_kernel(GSArgs a, int pass) {
+  extern __shared__ float4 scf[];                       // per column: {cv hi/lo}, {cw hi/lo}; then csm, big
   __shared__ double sh[32];
   __shared__ int s_skip;
   if (threadIdx.x == 0) s_skip = a.st->done;
   __syncthreads();
   if (s_skip) return;
   const int j = a.j;
-  for (int i = threadIdx.x; i <= j; i += kThreads) {
-    const coef4 c = a.coef[i];
-    scf[2 * i] = split(make_double2(c.vr, c.vi));
-    scf[2 * i + 1] = split(make_double2(c.wr, c.wi));
-  }
+  UpdCoef u{scf, scf + 2 * (j + 1), (unsigned char*)(scf + 3 * (j + 1))};
+  classify_coefs(a.coef, j, a.st->nrm[pass - 1], u);   // ||y|| before this update (b0, or the last pass's)
   if (blockIdx.x == 0 && threadIdx.x == 0) a.st->units_update += (double)(j + 1) * (double)a.h;
   __syncthreads();
   const int64_t p0 = (int64_t)blockIdx.x * a.rows_per_block;
   const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, a.h);
   __shared__ float red_s[kGroups][32][4], red_e[kGroups][32][4];
-  const double nrm = block_sum(dfupdate_rows(a, p0, p1, scf, red_s, red_e), sh);
+  const double nrm = block_sum(dfupdate_rows(a, p0, p1, u, red_s, red_e), sh);
   if (threadIdx.x == 0) a.part_nrm[blockIdx.x] = nrm;
 }
 
@@ -469,6 +516,7 @@ gsdf_step_coop_kernel(GSArgs a, double2* __restrict__ x, const double2* __restri
   float4* ys = (float4*)dyn;
   float* red = (float*)(ys + 2 * a.rows_per_block);
   float4* scf = (float4*)(red + kGroups * 2 * (4 * kCols) * 33);
+  const UpdCoef upd{scf, scf + 2 * (a.m + 1), (unsigned char*)(scf + 3 * (a.m + 1))};
   const int j = a.j;
   const int64_t h = a.h;
   const int nblk = a.nblk;
@@ -532,17 +580,13 @@ gsdf_step_coop_kernel(GSArgs a, double2* __restrict__ x, const double2* __restri
       }
     }
     grid.sync();
-    for (int i = threadIdx.x; i <= j; i += kThreads) {
-      const coef4 cc = a.coef[i];
-      scf[2 * i] = split(make_double2(cc.vr, cc.vi));
-      scf[2 * i + 1] = split(make_double2(cc.wr, cc.wi));
-    }
+    classify_coefs(a.coef, j, bref, upd);                 // bref: ||y|| before this update
     __syncthreads();
     double* slot = nrm2 + (size_t)(pass & 1) * nblk;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
       const int64_t p0 = (int64_t)rb * a.rows_per_block;
       const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
-      const double nb = block_sum(dfupdate_rows(a, p0, p1, scf, red_s, red_e), sh);
+      const double nb = block_sum(dfupdate_rows(a, p0, p1, upd, red_s, red_e), sh);
       if (threadIdx.x == 0) slot[rb] = nb;
     }
     if (lead) st->units_update += (double)(j + 1) * (double)h;
@@ -720,7 +764,21 @@ __device__ __forceinline__ void cdf_accc(float* s, float* e, float4 a, float4 b)
   df_acc(s[1], e[1], a.x, a.z, b.y, b.w);
   df_sub(s[1], e[1], a.y, a.w, b.x, b.z);
 }
+// The same for a link exact in FP32 (a = (re, im), no low part).
+__device__ __forceinline__ void cdf_acc(float* s, float* e, float2 a, float4 b) {
+  df_acc_xa(s[0], e[0], a.x, b.x, b.z);
+  df_acc_xa(s[0], e[0], -a.y, b.y, b.w);
+  df_acc_xa(s[1], e[1], a.x, b.y, b.w);
+  df_acc_xa(s[1], e[1], a.y, b.x, b.z);
+}
+__device__ __forceinline__ void cdf_accc(float* s, float* e, float2 a, float4 b) {
+  df_acc_xa(s[0], e[0], a.x, b.x, b.z);
+  df_acc_xa(s[0], e[0], a.y, b.y, b.w);
+  df_acc_xa(s[1], e[1], a.x, b.y, b.w);
+  df_acc_xa(s[1], e[1], -a.y, b.x, b.z);
+}
 __device__ __forceinline__ float4 cneg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
 
 // The hopping sums of site s, colour a, in compensated FP32: (ys1, ye1) and (ys2, ye2) for the U
 // terms of y1 and y2, (ws1, we1) and (ws2, we2) for the W terms (kappa not yet applied).
@@ -728,10 +786,8 @@ struct DfSums {
   float ys1[2], ye1[2], ys2[2], ye2[2], ws1[2], we1[2], ws2[2], we2[2];
 };
 
-// A link as a (hi, lo) pair: either stored so, or exact in FP32 (lo = 0, which the compiler folds
-// out of every product).
-__device__ __forceinline__ float4 link4(float4 l) { return l; }
-__device__ __forceinline__ float4 link4(float2 l) { return make_float4(l.x, l.y, 0.f, 0.f); }
+// A link as stored: a (hi, lo) float4 pair, or a float2 exact in FP32 (complex64 links), for which
+// the products take the shorter exact-multiplier form.
 
 template <typename LinkT>
 __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* __restrict__ x, int s, int a,
@@ -765,10 +821,10 @@ __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* _
     for (int b = 0; b < 3; ++b) {
       const float4 p1 = x1[3 * sp + b], p2 = x2[3 * sp + b];
       const float4 m1 = x1[3 * sm + b], m2 = x2[3 * sm + b];
-      const float4 uf = link4(Um[(a * 3 + b) * vol + s]);    // U(s)_{ab}
-      const float4 ub = link4(Um[(b * 3 + a) * vol + sm]);   // U(s-mu)_{ba}
-      const float4 wf = link4(Wm[(a * 3 + b) * vol + s]);    // W(s)_{ab}
-      const float4 wb = link4(Wm[(b * 3 + a) * vol + sm]);   // W(s-mu)_{ba}
+      const LinkT uf = Um[(a * 3 + b) * vol + s];    // U(s)_{ab}
+      const LinkT ub = Um[(b * 3 + a) * vol + sm];   // U(s-mu)_{ba}
+      const LinkT wf = Wm[(a * 3 + b) * vol + s];    // W(s)_{ab}
+      const LinkT wb = Wm[(b * 3 + a) * vol + sm];   // W(s-mu)_{ba}
       cdf_acc(r.ys1, r.ye1, uf, p1);           // U(s) x1(s+mu)
       cdf_accc(r.ys1, r.ye1, ub, m1);          // U(s-mu)^H x1(s-mu)
       cdf_accc(r.ys2, r.ye2, uf, p2);          // U(s)^* x2(s+mu)
@@ -943,7 +999,9 @@ cudaError_t launch_gsdf_first(const GSArgs& a, const void* x, const double2* alp
   return cudaGetLastError();
 }
 
-size_t gsdf_coop_smem(const GSArgs& a) { return dot_smem(a) + (size_t)2 * (a.m + 1) * sizeof(float4); }
+size_t gsdf_coop_smem(const GSArgs& a) {
+  return dot_smem(a) + (size_t)3 * (a.m + 1) * sizeof(float4) + (size_t)(a.m + 1);
+}
 
 cudaError_t gsdf_coop_occupancy(const GSArgs& a, int* per_sm) {
   int dev = 0, coop = 0, per = 0;
@@ -980,8 +1038,9 @@ cudaError_t launch_gsdf_dot(const GSArgs& a, int pass, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gsdf_update(const GSArgs& a, cudaStream_t s) {
-  gsdf_update_kernel<<<a.nblk, kThreads, (size_t)(a.j + 1) * 2 * sizeof(float4), s>>>(a);
+cudaError_t launch_gsdf_update(const GSArgs& a, int pass, cudaStream_t s) {
+  const size_t sm = (size_t)(a.j + 1) * 3 * sizeof(float4) + (size_t)(a.j + 1);
+  gsdf_update_kernel<<<a.nblk, kThreads, sm, s>>>(a, pass);
   return cudaGetLastError();
 }
 

@@ -76,7 +76,7 @@ cudaError_t launch_gs_normalize(const GSArgs& a, cudaStream_t s);
 cudaError_t launch_gsdf_first(const GSArgs& a, const void* x, const double2* alpha_part, int n_alpha_part,
                               cudaStream_t s);
 cudaError_t launch_gsdf_dot(const GSArgs& a, int pass, cudaStream_t s);
-cudaError_t launch_gsdf_update(const GSArgs& a, cudaStream_t s);
+cudaError_t launch_gsdf_update(const GSArgs& a, int pass, cudaStream_t s);   // pass: 1 after the first dots
 cudaError_t launch_gsdf_normalize(const GSArgs& a, void* x, cudaStream_t s);
 cudaError_t launch_df_from_fp64(const void* in, void* out, int64_t n, cudaStream_t s);
 cudaError_t launch_fp64_from_df(const void* in, void* out, int64_t n, cudaStream_t s);
