@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libjtrlan.so")
-SOURCES = ["matvec.cu", "gs.cu", "gsdf.cu", "ritz.cu", "api.cu", "noalloc.cu", "batch.cu", "batch_api.cu", "filter.cu", "mlp.cu", "rotate_tc.cu", "cg.cu", "peaks.cu"]
+SOURCES = ["matvec.cu", "gs.cu", "gsdf.cu", "ritz.cu", "api.cu", "noalloc.cu", "batch.cu", "batch_api.cu", "filter.cu", "mlp.cu", "rotate_tc.cu", "cg.cu", "peaks.cu", "launch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

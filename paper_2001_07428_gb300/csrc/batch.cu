@@ -282,16 +282,16 @@ __device__ void cta_matvec_df1(const float4* A11, const float4* A12, int64_t h, 
   }
 }
 
-template <bool DF>
+template <bool DF, int MVR>
 __device__ void cta_matvec(const BatchArgs& a, int64_t h, int64_t off, const double2* x, const float4* x4, double2* y,
                            double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if constexpr (DF) {
-    if (a.mv_rows == 1)
+    if constexpr (MVR == 1)
       cta_matvec_df1((const float4*)a.A11 + off, (const float4*)a.A12 + off, h, x4, y);
     else
       cta_matvec_df((const float4*)a.A11 + off, (const float4*)a.A12 + off, h, x4, y);
-  } else if (a.mv_rows == 2) {   // two rows per warp (r and r + nw) sharing the loads of x
+  } else if constexpr (MVR == 2) {   // two rows per warp (r and r + nw) sharing the loads of x
     for (int64_t r = w; r < h; r += 2 * nw) {
       const int64_t r2 = r + nw;
       const bool two = r2 < h;
@@ -894,7 +894,9 @@ __device__ void cta_jacobi(const double* T, int ld, int m, int kk, int which, do
   __syncthreads();
 }
 
-template <bool DF>
+// MVR: rows of the product a warp takes at once (the tile shape jtrlan_batch_set_tiles selects; a
+// template parameter, so that each instance holds one code path and its registers).
+template <bool DF, int MVR>
 __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Shared S;
@@ -960,7 +962,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(BatchArgs a) {
           }
         }
         __syncthreads();
-        cta_matvec<DF>(a, h, off, x, x4, y, S.red);
+        cta_matvec<DF, MVR>(a, h, off, x, x4, y, S.red);
         ++n_mv;
         double al = 0.0;
         for (int64_t p = threadIdx.x; p < n; p += blockDim.x) al += x[p].x * y[p].x + x[p].y * y[p].y;
@@ -1065,7 +1067,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(BatchArgs a) {
           if (DF) x4[p] = b_split(v);
         }
         __syncthreads();
-        cta_matvec<DF>(a, h, off, x, x4, y, S.red);
+        cta_matvec<DF, MVR>(a, h, off, x, x4, y, S.red);
         ++n_res;
         double rr = 0.0;
         for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
@@ -1200,18 +1202,29 @@ __global__ void c64_to_c128_batch_kernel(const float2* in, double2* out, int64_t
 
 size_t batch_smem_bytes(int64_t nmax, int m, int kk, int threads) { return BatchSmem(nmax, m, kk, threads).total; }
 
-cudaError_t batch_occupancy(bool df, int threads, size_t smem, int* blocks) {
-  cudaError_t e = df ? cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                     : cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+namespace {
+const void* batch_fn(bool df, int mv_rows) {
+  if (df) return mv_rows == 1 ? (const void*)batch_kernel<true, 1> : (const void*)batch_kernel<true, 2>;
+  return mv_rows == 2 ? (const void*)batch_kernel<false, 2> : (const void*)batch_kernel<false, 1>;
+}
+}  // namespace
+
+cudaError_t batch_occupancy(bool df, int mv_rows, int threads, size_t smem, int* blocks) {
+  const void* f = batch_fn(df, mv_rows);
+  cudaError_t e = allow_dyn_smem(f, smem);
   if (e != cudaSuccess) return e;
-  return df ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<true>, threads, smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<false>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem);
 }
 
 cudaError_t launch_batch(bool df, const BatchArgs& a, int grid, int threads, cudaStream_t s) {
   const size_t sm = batch_smem_bytes(a.nmax, a.m, a.kk, threads);
-  if (df) batch_kernel<true><<<grid, threads, sm, s>>>(a);
-  else batch_kernel<false><<<grid, threads, sm, s>>>(a);
+  if (df) {
+    if (a.mv_rows == 1) batch_kernel<true, 1><<<grid, threads, sm, s>>>(a);
+    else batch_kernel<true, 2><<<grid, threads, sm, s>>>(a);
+  } else {
+    if (a.mv_rows == 2) batch_kernel<false, 2><<<grid, threads, sm, s>>>(a);
+    else batch_kernel<false, 1><<<grid, threads, sm, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

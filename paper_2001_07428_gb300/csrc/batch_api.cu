@@ -217,6 +217,8 @@ jtrlan_status create_batch(int count, const jtrlan_operator* ops, const jtrlan_p
 }
 
 // Launch shape for (threads, ctas_per_sm): one resident wave of CTAs, no more than there are instances.
+BatchArgs args_of(const jtrlan_batch* b);
+
 jtrlan_status shape(jtrlan_batch* b, int threads, int ctas_per_sm, int* grid) {
   const size_t sm = batch_smem_bytes(b->nmax, b->m, b->kk, threads);
   int dev = 0, optin = 0;
@@ -225,7 +227,7 @@ jtrlan_status shape(jtrlan_batch* b, int threads, int ctas_per_sm, int* grid) {
   if (sm + 8192 > (size_t)optin)
     return bfail(JTRLAN_EINVAL, "the largest instance needs more shared memory per CTA than the device has");
   int fit = 0;
-  JB_CUDA(batch_occupancy(b->df, threads, sm, &fit));
+  JB_CUDA(batch_occupancy(b->df, args_of(b).mv_rows, threads, sm, &fit));
   if (fit < 1) return bfail(JTRLAN_EINVAL, "the batched kernel does not fit on an SM at this size");
   const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, fit) : fit;
   *grid = std::max(1, std::min(b->count, per * b->n_sm));
@@ -358,7 +360,7 @@ jtrlan_status jtrlan_batch_tune(jtrlan_batch* b, int* threads_out, int* ctas_per
   float best = 3.4e38f;
   for (int t : cand_threads) {
     int fit = 0;
-    JB_CUDA(batch_occupancy(b->df, t, batch_smem_bytes(b->nmax, b->m, b->kk, t), &fit));
+    JB_CUDA(batch_occupancy(b->df, args_of(b).mv_rows, t, batch_smem_bytes(b->nmax, b->m, b->kk, t), &fit));
     for (int c = 1; c <= fit; ++c) {
       if ((c - 1) * b->n_sm >= b->count) break;  // the grid is capped at the instance count
       JB_TRY(run_once(b, t, c, false, &ms));

@@ -577,7 +577,7 @@ int gs_blocks(int64_t h, int* rows_per_block) {
 template <typename R>
 cudaError_t launch_gs_first(const GSArgs& a, const double2* alpha_part, int n_alpha_part, cudaStream_t s) {
   if (dot_smem<R>() > 48 * 1024) {  // per device, so set on every launch (cheap)
-    cudaError_t e = cudaFuncSetAttribute(gs_first_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dot_smem<R>());
+    cudaError_t e = allow_dyn_smem((const void*)gs_first_kernel<R>, (size_t)dot_smem<R>());
     if (e != cudaSuccess) return e;
   }
   gs_first_kernel<R><<<a.nblk, kGsThreads, dot_smem<R>(), s>>>(a, alpha_part, n_alpha_part);
@@ -598,7 +598,7 @@ cudaError_t launch_gs_update(const GSArgs& a, cudaStream_t s) {
 template <typename R>
 cudaError_t launch_gs_dot(const GSArgs& a, int pass, cudaStream_t s) {
   if (dot_smem<R>() > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gs_dot_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dot_smem<R>());
+    cudaError_t e = allow_dyn_smem((const void*)gs_dot_kernel<R>, (size_t)dot_smem<R>());
     if (e != cudaSuccess) return e;
   }
   gs_dot_kernel<R><<<a.nblk, kGsThreads, dot_smem<R>(), s>>>(a, pass);
@@ -661,7 +661,7 @@ cudaError_t gs_coop_occupancy(int m, int* per_sm) {
   if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
   const size_t sm = gs_coop_smem<R>(m);
-  if ((e = cudaFuncSetAttribute(gs_step_coop_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+  if ((e = allow_dyn_smem((const void*)gs_step_coop_kernel<R>, (size_t)sm)) !=
       cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gs_step_coop_kernel<R>, kGsThreads, sm)) != cudaSuccess)

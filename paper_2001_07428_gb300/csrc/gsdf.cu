@@ -22,10 +22,11 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kGroups = kThreads / 32;
-// Dot kernels: one column per warp chunk and at least 4 resident blocks per SM (measured best on
-// GB300 at 16^4: 2.2x faster than 8-column chunks at 2 blocks per SM).
+// Dot kernels: one column per warp chunk (measured best on GB300 at 16^4: 2.2x faster than 8-column
+// chunks).  Their shared memory (the split of y over a block's rows) holds them to two blocks per SM
+// on the largest lattices, so they may use up to 128 registers: room for the pipelined loads.
 constexpr int kCols = 1;             // columns per warp chunk in the dot kernels (4 * kCols <= 32)
-constexpr int kDotMinBlocks = 4;
+constexpr int kDotMinBlocks = 2;
 constexpr double kSqrt2 = 1.4142135623730951;
 
 // ------------------------------------------------------------------ error-free building blocks
@@ -35,15 +36,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) { 
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// (s, e) += sign * (ah + al) * (bh + bl), products split exactly, cross terms to first order.
+// (s, e) += (ah + al) * (bh + bl): ah * bh split exactly into the sum (TwoSum) and its rounding
+// error, the cross terms ah * bl and al * bh (first order) fused into the error sum -- 12 FP32 ops.
 __device__ __forceinline__ void df_acc(float& s, float& e, float ah, float al, float bh, float bl) {
   const float p = __fmul_rn(ah, bh);
   const float pe = __fmaf_rn(ah, bh, -p);
-  const float cross = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
   float t, te;
   two_sum(s, p, t, te);
   s = t;
-  e = __fadd_rn(e, __fadd_rn(te, __fadd_rn(pe, cross)));
+  e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fadd_rn(e, __fadd_rn(te, pe))));
 }
 __device__ __forceinline__ void df_sub(float& s, float& e, float ah, float al, float bh, float bl) {
   df_acc(s, e, -ah, -al, bh, bl);
@@ -72,88 +73,97 @@ __device__ __forceinline__ double2 join(float4 f) {
 // rows [p0, p1); y has been split into ys (shared, [2][rows]).  Warp q takes chunks of 8 columns;
 // each lane keeps 8 x 4 (sum, error) pairs, combines them to FP64 and the warp transposes them
 // through shared memory so that lane k adds up accumulator k.
+// 16 compensated products of one row pair (v1, v2) of a column with (y1, y2) into the four sums.
+__device__ __forceinline__ void dfdot_row(float* s, float* e, float4 v1, float4 v2, float4 y1, float4 y2) {
+  // Re c_v: v1.x y1.x + v1.y y1.y + v2.x y2.x + v2.y y2.y
+  df_acc(s[0], e[0], v1.x, v1.z, y1.x, y1.z);
+  df_acc(s[0], e[0], v1.y, v1.w, y1.y, y1.w);
+  df_acc(s[0], e[0], v2.x, v2.z, y2.x, y2.z);
+  df_acc(s[0], e[0], v2.y, v2.w, y2.y, y2.w);
+  // Im c_v: v1.x y1.y - v1.y y1.x + v2.x y2.y - v2.y y2.x
+  df_acc(s[1], e[1], v1.x, v1.z, y1.y, y1.w);
+  df_sub(s[1], e[1], v1.y, v1.w, y1.x, y1.z);
+  df_acc(s[1], e[1], v2.x, v2.z, y2.y, y2.w);
+  df_sub(s[1], e[1], v2.y, v2.w, y2.x, y2.z);
+  // Re c_w: v1.x y2.x - v1.y y2.y - v2.x y1.x + v2.y y1.y
+  df_acc(s[2], e[2], v1.x, v1.z, y2.x, y2.z);
+  df_sub(s[2], e[2], v1.y, v1.w, y2.y, y2.w);
+  df_sub(s[2], e[2], v2.x, v2.z, y1.x, y1.z);
+  df_acc(s[2], e[2], v2.y, v2.w, y1.y, y1.w);
+  // Im c_w: v1.x y2.y + v1.y y2.x - v2.x y1.y - v2.y y1.x
+  df_acc(s[3], e[3], v1.x, v1.z, y2.y, y2.w);
+  df_acc(s[3], e[3], v1.y, v1.w, y2.x, y2.z);
+  df_sub(s[3], e[3], v2.x, v2.z, y1.y, y1.w);
+  df_sub(s[3], e[3], v2.y, v2.w, y1.x, y1.z);
+}
+
+// ------------------------------------------------------------------ inner products (one pass)
+// c_v,i = sum_p conj(v1) y1 + conj(v2) y2 and c_w,i = sum_p (v1 y2 - v2 y1) for columns 0..j over
+// rows [p0, p1); y has been split into ys (shared, [2][rows]).  Warp q takes one column at a time
+// (q, q + 8, ...); each lane walks four rows at a time and keeps 4 (sum, error) pairs, combines them
+// to FP64 and the warp transposes them through shared memory so that lane k adds up accumulator k.
+// Pipelined (the separate launches, two blocks per SM): the next four rows' eight loads of V are
+// issued before the current four rows' arithmetic, so each warp keeps 8 KB in flight.
+template <bool Pipelined>
 __device__ void dfdot_body(const GSArgs& a, int64_t p0, int64_t p1, const float4* ys, float* red, int rb) {
+  static_assert(kCols == 1, "one column per warp chunk");
   const float4* V = (const float4*)a.V;
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   const int64_t n = a.n, h = a.h, rows = p1 - p0;
   float* wred_s = red + (size_t)q * 2 * (4 * kCols) * 33;   // sums, then rounding errors, [4 kCols][33]
   float* wred_e = wred_s + (4 * kCols) * 33;
-  for (int c0 = kCols * q; c0 <= a.j; c0 += kCols * kGroups) {
-    float s[kCols][4], e[kCols][4];
+  for (int c0 = q; c0 <= a.j; c0 += kGroups) {
+    float s[1][4], e[1][4];
 #pragma unroll
-    for (int c = 0; c < kCols; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) s[c][t] = e[c][t] = 0.f;
-    const int ncol = min(kCols, a.j + 1 - c0);
-    // four rows per lane: their eight loads of V are issued before the arithmetic, so a warp keeps
-    // 4 KB in flight (the basis is read from HBM once per pass and the y tile sits in shared memory)
+    for (int t = 0; t < 4; ++t) s[0][t] = e[0][t] = 0.f;
+    const int ncol = 1;
+    const float4* vi = V + (int64_t)c0 * n + p0;
     int64_t r0 = lane;
-    for (; r0 + 96 < rows; r0 += 128) {
+    if (Pipelined) {
+      if (r0 + 96 < rows) {
+        float4 a1[4], a2[4];
 #pragma unroll
-      for (int c = 0; c < kCols; ++c) {
-        if (c < ncol) {
-          const float4* vi = V + (int64_t)(c0 + c) * n + p0;
-          float4 v1u[4], v2u[4];
+        for (int u = 0; u < 4; ++u) {
+          a1[u] = vi[r0 + 32 * u];
+          a2[u] = vi[h + r0 + 32 * u];
+        }
+        for (;;) {
+          const int64_t rn = r0 + 128;
+          const bool more = rn + 96 < rows;
+          float4 b1[4], b2[4];
+          if (more) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            v1u[u] = vi[r0 + 32 * u];
-            v2u[u] = vi[h + r0 + 32 * u];
+            for (int u = 0; u < 4; ++u) {
+              b1[u] = vi[rn + 32 * u];
+              b2[u] = vi[h + rn + 32 * u];
+            }
           }
 #pragma unroll
+          for (int u = 0; u < 4; ++u) dfdot_row(s[0], e[0], a1[u], a2[u], ys[r0 + 32 * u], ys[rows + r0 + 32 * u]);
+          r0 = rn;
+          if (!more) break;
+#pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const float4 y1 = ys[r0 + 32 * u], y2 = ys[rows + r0 + 32 * u];
-            const float4 v1 = v1u[u], v2 = v2u[u];
-            df_acc(s[c][0], e[c][0], v1.x, v1.z, y1.x, y1.z);
-            df_acc(s[c][0], e[c][0], v1.y, v1.w, y1.y, y1.w);
-            df_acc(s[c][0], e[c][0], v2.x, v2.z, y2.x, y2.z);
-            df_acc(s[c][0], e[c][0], v2.y, v2.w, y2.y, y2.w);
-            df_acc(s[c][1], e[c][1], v1.x, v1.z, y1.y, y1.w);
-            df_sub(s[c][1], e[c][1], v1.y, v1.w, y1.x, y1.z);
-            df_acc(s[c][1], e[c][1], v2.x, v2.z, y2.y, y2.w);
-            df_sub(s[c][1], e[c][1], v2.y, v2.w, y2.x, y2.z);
-            df_acc(s[c][2], e[c][2], v1.x, v1.z, y2.x, y2.z);
-            df_sub(s[c][2], e[c][2], v1.y, v1.w, y2.y, y2.w);
-            df_sub(s[c][2], e[c][2], v2.x, v2.z, y1.x, y1.z);
-            df_acc(s[c][2], e[c][2], v2.y, v2.w, y1.y, y1.w);
-            df_acc(s[c][3], e[c][3], v1.x, v1.z, y2.y, y2.w);
-            df_acc(s[c][3], e[c][3], v1.y, v1.w, y2.x, y2.z);
-            df_sub(s[c][3], e[c][3], v2.x, v2.z, y1.y, y1.w);
-            df_sub(s[c][3], e[c][3], v2.y, v2.w, y1.x, y1.z);
+            a1[u] = b1[u];
+            a2[u] = b2[u];
           }
         }
       }
-    }
-    for (int64_t r = r0; r < rows; r += 32) {
-      const float4 y1 = ys[r], y2 = ys[rows + r];
-      const int64_t p = p0 + r;
+    } else {
+      // four rows per lane: their eight loads of V are issued before the arithmetic, so a warp keeps
+      // 4 KB in flight (the basis is read from HBM once per pass and the y tile sits in shared memory)
+      for (; r0 + 96 < rows; r0 += 128) {
+        float4 v1u[4], v2u[4];
 #pragma unroll
-      for (int c = 0; c < kCols; ++c) {
-        if (c < ncol) {
-          const float4* vi = V + (int64_t)(c0 + c) * n;
-          const float4 v1 = vi[p], v2 = vi[h + p];
-          // Re c_v: v1.x y1.x + v1.y y1.y + v2.x y2.x + v2.y y2.y
-          df_acc(s[c][0], e[c][0], v1.x, v1.z, y1.x, y1.z);
-          df_acc(s[c][0], e[c][0], v1.y, v1.w, y1.y, y1.w);
-          df_acc(s[c][0], e[c][0], v2.x, v2.z, y2.x, y2.z);
-          df_acc(s[c][0], e[c][0], v2.y, v2.w, y2.y, y2.w);
-          // Im c_v: v1.x y1.y - v1.y y1.x + v2.x y2.y - v2.y y2.x
-          df_acc(s[c][1], e[c][1], v1.x, v1.z, y1.y, y1.w);
-          df_sub(s[c][1], e[c][1], v1.y, v1.w, y1.x, y1.z);
-          df_acc(s[c][1], e[c][1], v2.x, v2.z, y2.y, y2.w);
-          df_sub(s[c][1], e[c][1], v2.y, v2.w, y2.x, y2.z);
-          // Re c_w: v1.x y2.x - v1.y y2.y - v2.x y1.x + v2.y y1.y
-          df_acc(s[c][2], e[c][2], v1.x, v1.z, y2.x, y2.z);
-          df_sub(s[c][2], e[c][2], v1.y, v1.w, y2.y, y2.w);
-          df_sub(s[c][2], e[c][2], v2.x, v2.z, y1.x, y1.z);
-          df_acc(s[c][2], e[c][2], v2.y, v2.w, y1.y, y1.w);
-          // Im c_w: v1.x y2.y + v1.y y2.x - v2.x y1.y - v2.y y1.x
-          df_acc(s[c][3], e[c][3], v1.x, v1.z, y2.y, y2.w);
-          df_acc(s[c][3], e[c][3], v1.y, v1.w, y2.x, y2.z);
-          df_sub(s[c][3], e[c][3], v2.x, v2.z, y1.y, y1.w);
-          df_sub(s[c][3], e[c][3], v2.y, v2.w, y1.x, y1.z);
+        for (int u = 0; u < 4; ++u) {
+          v1u[u] = vi[r0 + 32 * u];
+          v2u[u] = vi[h + r0 + 32 * u];
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dfdot_row(s[0], e[0], v1u[u], v2u[u], ys[r0 + 32 * u], ys[rows + r0 + 32 * u]);
       }
     }
+    for (int64_t r = r0; r < rows; r += 32) dfdot_row(s[0], e[0], vi[r], vi[h + r], ys[r], ys[rows + r]);
 #pragma unroll
     for (int c = 0; c < kCols; ++c)
 #pragma unroll
@@ -233,7 +243,7 @@ gsdf_first_kernel(GSArgs a, const double2* __restrict__ x, const double2* __rest
   float4* ys = (float4*)dyn;
   float* red = (float*)(ys + 2 * a.rows_per_block);
   split_rows(a, p0, p1, ys);
-  dfdot_body(a, p0, p1, ys, red, blockIdx.x);
+  dfdot_body<true>(a, p0, p1, ys, red, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kThreads, kDotMinBlocks) gsdf_dot_kernel(GSArgs a, int pass) {
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, kDotMinBlocks) gsdf_dot_kernel(GSArg
   float4* ys = (float4*)dyn;
   float* red = (float*)(ys + 2 * a.rows_per_block);
   split_rows(a, p0, p1, ys);
-  dfdot_body(a, p0, p1, ys, red, blockIdx.x);
+  dfdot_body<true>(a, p0, p1, ys, red, blockIdx.x);
 }
 
 // The update's coefficients in shared memory, classified once per launch (every block alike):
@@ -556,7 +566,7 @@ gsdf_step_coop_kernel(GSArgs a, double2* __restrict__ x, const double2* __restri
     nrm = block_sum(nrm, sh);
     if (threadIdx.x == 0) nrm2[rb] = nrm;
     split_rows(a, p0, p1, ys);
-    dfdot_body(a, p0, p1, ys, red, rb);
+    dfdot_body<false>(a, p0, p1, ys, red, rb);
     __syncthreads();                                       // ys and red are reused by the next row block
   }
   double bref = 0.0, beta = 0.0;
@@ -606,7 +616,7 @@ gsdf_step_coop_kernel(GSArgs a, double2* __restrict__ x, const double2* __restri
       const int64_t p0 = (int64_t)rb * a.rows_per_block;
       const int64_t p1 = min(p0 + (int64_t)a.rows_per_block, h);
       split_rows(a, p0, p1, ys);
-      dfdot_body(a, p0, p1, ys, red, rb);
+      dfdot_body<false>(a, p0, p1, ys, red, rb);
       __syncthreads();
     }
   }
@@ -804,6 +814,9 @@ __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* _
     r.ws1[c] = r.we1[c] = r.ws2[c] = r.we2[c] = 0.f;
   }
   const int d0 = op.dims[0], d1 = op.dims[1], d2 = op.dims[2], d3 = op.dims[3];
+  // the site's coordinates, once (x fastest)
+  const int r1 = s / d0, r2 = r1 / d1;
+  const int x0 = s - r1 * d0, x1c = r1 - r2 * d1, x2c = r2 % d2, x3c = r2 / d2;
   int stride = 1;
   // the direction loop stays rolled: unrolled, its 4 x 3 x 8 compensated products overflowed the
   // instruction cache (ncu: "no instruction" stalls as frequent as memory stalls); extents and
@@ -811,7 +824,7 @@ __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* _
 #pragma unroll 1
   for (int mu = 0; mu < 4; ++mu) {
     const int L = mu == 0 ? d0 : mu == 1 ? d1 : mu == 2 ? d2 : d3;
-    const int c = (s / stride) % L;
+    const int c = mu == 0 ? x0 : mu == 1 ? x1c : mu == 2 ? x2c : x3c;
     const int sp = (c == L - 1) ? s - (L - 1) * stride : s + stride;
     const int sm = (c == 0) ? s + (L - 1) * stride : s - stride;
     stride *= L;
@@ -993,7 +1006,7 @@ size_t dot_smem(const GSArgs& a) {
 cudaError_t launch_gsdf_first(const GSArgs& a, const void* x, const double2* alpha_part, int n_alpha_part,
                               cudaStream_t s) {
   const size_t sm = dot_smem(a);
-  cudaError_t e = cudaFuncSetAttribute(gsdf_first_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dyn_smem((const void*)gsdf_first_kernel, (size_t)sm);
   if (e != cudaSuccess) return e;
   gsdf_first_kernel<<<a.nblk, kThreads, sm, s>>>(a, (const double2*)x, alpha_part, n_alpha_part);
   return cudaGetLastError();
@@ -1009,7 +1022,7 @@ cudaError_t gsdf_coop_occupancy(const GSArgs& a, int* per_sm) {
   if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
   const size_t sm = gsdf_coop_smem(a);
-  if ((e = cudaFuncSetAttribute(gsdf_step_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+  if ((e = allow_dyn_smem((const void*)gsdf_step_coop_kernel, (size_t)sm)) !=
       cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gsdf_step_coop_kernel, kThreads, sm)) != cudaSuccess)
@@ -1032,7 +1045,7 @@ cudaError_t launch_gsdf_step_coop(const GSArgs& a, void* x, const double2* alpha
 
 cudaError_t launch_gsdf_dot(const GSArgs& a, int pass, cudaStream_t s) {
   const size_t sm = dot_smem(a);
-  cudaError_t e = cudaFuncSetAttribute(gsdf_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dyn_smem((const void*)gsdf_dot_kernel, (size_t)sm);
   if (e != cudaSuccess) return e;
   gsdf_dot_kernel<<<a.nblk, kThreads, sm, s>>>(a, pass);
   return cudaGetLastError();

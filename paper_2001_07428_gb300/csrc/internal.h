@@ -9,6 +9,11 @@
 
 namespace jtr {
 
+// Allows `bytes` of dynamic shared memory for kernel `func` on the current device: raises the
+// kernel's cap once per device to the opt-in maximum (thread-safe); cudaErrorInvalidValue if `bytes`
+// exceeds that maximum.
+cudaError_t allow_dyn_smem(const void* func, size_t bytes);
+
 // Description of the operator as the kernels see it (device pointers owned by the context).
 struct OpDev {
   int kind;            // JTRLAN_DENSE / JTRLAN_STENCIL4D
@@ -224,7 +229,7 @@ constexpr int kBatchMaxM = 64;
 constexpr int kBatchMaxNev = 32;
 constexpr int kBatchMaxThreads = 512;
 size_t batch_smem_bytes(int64_t nmax, int m, int kk, int threads);
-cudaError_t batch_occupancy(bool df, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t batch_occupancy(bool df, int mv_rows, int threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_batch(bool df, const BatchArgs& a, int grid, int threads, cudaStream_t s);
 // In place: each double2 element becomes the float4 (hi.re, hi.im, lo.re, lo.im) with hi = fl32(x),
 // lo = fl32(x - hi).

@@ -348,7 +348,7 @@ cudaError_t launch_ritz(const double* T, int ldt, int m, int k, int kk, int whic
   int* fallback = flags;      // 1: run the Jacobi kernel
   const size_t bsm = (size_t)kBisectWarps * 3 * m * sizeof(double);
   if (bsm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(ritz_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+    cudaError_t e = allow_dyn_smem((const void*)ritz_bisect_kernel, (size_t)bsm);
     if (e != cudaSuccess) return e;
   }
   ritz_bisect_kernel<<<(kk + kBisectWarps - 1) / kBisectWarps, 32 * kBisectWarps, bsm, s>>>(T, ldt, m, k, kk, which, lam,
@@ -364,8 +364,7 @@ static cudaError_t jacobi_launch(const double* T, int ldt, int m, int which, dou
   const size_t bytes = (size_t)2 * mp * mp * sizeof(double);
   const int use_smem = bytes <= 160 * 1024;
   if (use_smem) {
-    cudaError_t e = cudaFuncSetAttribute(ritz_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+    cudaError_t e = allow_dyn_smem((const void*)ritz_jacobi_kernel, (size_t)bytes);
     if (e != cudaSuccess) return e;
   }
   ritz_jacobi_kernel<<<1, kRitzThreads, use_smem ? bytes : 0, s>>>(T, ldt, m, which, lam, Z, work, use_smem, gate,

@@ -503,7 +503,7 @@ cudaError_t launch_rotate_tc(const void* V, int64_t n, int m, const double* Z, i
   size_t smem = fixed + (size_t)nst * kStageA;
   if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: each holds all 512 tensor-memory columns
   {
-    cudaError_t e = cudaFuncSetAttribute(rotate_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    cudaError_t e = allow_dyn_smem((const void*)rotate_tc_kernel, smem);
     if (e != cudaSuccess) return e;
   }
   const int ngrp = (int)std::min<int64_t>(std::max(1, nsm / ntn), mtiles);

@@ -6,8 +6,10 @@ nev -- to the DEGREE + 1 Chebyshev coefficients g_0..g_DEGREE of a real filter p
 solver (JTRLAN_MIXED_REORTH: FP64 vectors, compensated-FP32 products and Gram-Schmidt) runs Algorithm 1
 on B = p(A) and accepts a pair only when the true residual of A at x^H A x is below tol, so the plain
 method's criterion judges every answer, and the unfiltered solve is the fallback (solve_learned reruns
-it if the filtered solve fails).  Degree 16 (out of the <= 64 allowed) was the fastest of 8, 16, 32
-on 8^4, 12^4 and 16^4 lattices.
+it if the filtered solve fails).  Degree 64, the most allowed, was the fastest of 16, 24, 32, 48 and
+64 on the 24^3 x 48 lattice (nev 100, m 200): a sharper step separates the dense wanted cluster in
+fewer Lanczos steps, and each step's Gram-Schmidt against up to 200 columns costs more than the extra
+products.  A filter of lower degree with the same cut is one call away (at_degree).
 
 Training targets come from plain runs of the method: the lowest nev + 1 eigenvalues give the cut
 (lambda_nev + lambda_{nev+1})/2, whose Jackson-damped step (jtrlan_damped_step) is the target.
@@ -29,7 +31,7 @@ from . import binding as B
 PKG = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(PKG, "filter_mlp.npz")
 RUNS = os.path.join(PKG, "filter_runs.json")   # the plain runs the network was trained on
-DEGREE = 16
+DEGREE = 64
 WIDTH = 128
 N_FEATURES = 6
 BOUNDS_STEPS = 30
@@ -114,13 +116,25 @@ class FilterNet:
             pass
 
 
-def damped_targets(taus, device="cuda") -> np.ndarray:
-    """Jackson-damped step coefficients for each tau, from the library kernel."""
+def damped_targets(taus, device="cuda", degree=DEGREE) -> np.ndarray:
+    """Jackson-damped step coefficients of the given degree for each tau, from the library kernel."""
     td = torch.from_numpy(np.ascontiguousarray(taus, dtype=np.float64)).to(device)
-    out = torch.empty((len(taus), DEGREE + 1), dtype=torch.float32, device=device)
-    B.jtrlan_damped_step(td.data_ptr(), len(taus), DEGREE, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    out = torch.empty((len(taus), degree + 1), dtype=torch.float32, device=device)
+    B.jtrlan_damped_step(td.data_ptr(), len(taus), degree, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     return out.cpu().numpy()
+
+
+def cut_of(coeffs) -> float:
+    """The cut tau encoded by a damped step's coefficients: g_0 = (pi - acos tau)/pi."""
+    return float(np.cos(np.pi * (1.0 - np.asarray(coeffs)[0])))
+
+
+def at_degree(coeffs, degree, device="cuda") -> np.ndarray:
+    """The network's filter at another degree: the Jackson-damped step with the same cut."""
+    if degree == len(coeffs) - 1:
+        return np.asarray(coeffs, dtype=np.float64)
+    return damped_targets([cut_of(coeffs)], device, degree)[0].astype(np.float64)
 
 
 def stencil_bounds(U, W, dims, m0, kappa, device="cuda"):
@@ -142,13 +156,16 @@ def learned_filter(net: FilterNet, U, W, dims, m0, kappa, nev, device="cuda"):
     return g, window(lo, hi), f
 
 
-def filter_on_context(net: FilterNet, ctx, m0, kappa, nev, sites):
+def filter_on_context(net: FilterNet, ctx, m0, kappa, nev, sites, degree=None):
     """The learned filter for the operator of an existing context, set on that context: jtrlan_bounds
     on the context itself, network inference, jtrlan_set_filter.  Returns (coefficients, window,
-    features); the next jtrlan_solve of the context runs on B = p(A)."""
+    features); the next jtrlan_solve of the context runs on B = p(A).  degree: the filter's degree
+    if not the network's own (the damped step with the predicted cut)."""
     lo, hi = B.jtrlan_bounds(ctx, BOUNDS_STEPS)
     f = features(lo, hi, m0, kappa, nev, sites)
     g = net.predict(f[None, :])[0]
+    if degree:
+        g = at_degree(g, degree, net.device)
     win = window(lo, hi)
     B.jtrlan_set_filter(ctx, g, win)
     return g, win, f

@@ -62,3 +62,11 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = types.SimpleNamespace(workload="stencil_8x8x8x8", steps=1, warmup=0, gpus=2)
     bench.run_reference(args, rank=1, world=2)       # returns before any oracle work
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_of_the_largest_workload_runs_on_rank_zero_only(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    args = types.SimpleNamespace(workload=bench.HEADLINE, steps=1, warmup=0, gpus=2)
+    bench.run_reference_headline(args, rank=1, world=2)   # returns before any oracle work
+    assert capsys.readouterr().out == ""
