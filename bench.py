@@ -89,6 +89,9 @@ BYTES_PER_UNIT = {"matvec": 84 * 16.0, "resid": 84 * 16.0, "gs_first": 32.0, "gs
 # SHA-256 of the source file the capture was built from: the figure is reported only while that file
 # is unchanged (roofline.traffic is null otherwise).
 NCU_TRAFFIC = {
+    "matvec": dict(bytes=687.6e6, workload="stencil_24x24x24x48", kernel="stencil_df_cheb_kernel<float2> (middle step)",
+                   source="paper_2001_07428_gb300/csrc/gsdf.cu",
+                   sha256="e7dd4f02ac124e32d7db1998d3d07f30b666cf80e243739e4e04334593b75b83"),
     "gs_step": dict(bytes=13.66e6, workload="stencil_8x8x8x8", kernel="gs_step_coop_kernel<double>",
                     source="paper_2001_07428_gb300/csrc/gs.cu",
                     sha256="25f4b188216fe6b311d90026b3e55046646e3a430ba0d7a2b9d8b809fdae98b5"),

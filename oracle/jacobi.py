@@ -38,7 +38,10 @@ def jacobi_eigh(T, eps=1e-15, max_sweeps=60):
                 if apq == 0.0:
                     continue
                 tau = (A[q, q] - A[p, p]) / (2.0 * apq)
-                t = (1.0 if tau >= 0.0 else -1.0) / (abs(tau) + np.sqrt(1.0 + tau * tau))
+                if abs(tau) > 1e150:       # tau^2 would overflow; t -> 1/(2 tau) in that limit
+                    t = 0.5 / tau
+                else:
+                    t = (1.0 if tau >= 0.0 else -1.0) / (abs(tau) + np.sqrt(1.0 + tau * tau))
                 c = 1.0 / np.sqrt(1.0 + t * t)
                 s = t * c
                 # A := J^T A J with J the identity except J[p,p] = J[q,q] = c, J[p,q] = s, J[q,p] = -s

@@ -11,8 +11,9 @@ it if the filtered solve fails).  Degree 64, the most allowed, was the fastest o
 fewer Lanczos steps, and each step's Gram-Schmidt against up to 200 columns costs more than the extra
 products.  A filter of lower degree with the same cut is one call away (at_degree).
 
-Training targets come from plain runs of the method: the lowest nev + 1 eigenvalues give the cut
-(lambda_nev + lambda_{nev+1})/2, whose Jackson-damped step (jtrlan_damped_step) is the target.
+Training targets come from plain runs of the method: lambda_nev places the cut CUT_OFFSET transition
+widths below it, and the Jackson-damped step (jtrlan_damped_step) with that cut is the target.  The
+solver takes the exact damped step at the cut the network predicts (at_degree).
 
 Everything here is marshalling and bookkeeping on a few scalars per problem; every vector operation,
 the network and its training run in the library's kernels.
@@ -33,7 +34,7 @@ WEIGHTS = os.path.join(PKG, "filter_mlp.npz")
 RUNS = os.path.join(PKG, "filter_runs.json")   # the plain runs the network was trained on
 DEGREE = 64
 WIDTH = 128
-N_FEATURES = 6
+N_FEATURES = 5
 BOUNDS_STEPS = 30
 NEV_GRID = (8, 10, 12, 16, 20, 25, 30, 40, 50, 60, 70, 80, 90, 100)
 
@@ -44,16 +45,33 @@ def window(lo: float, hi: float):
 
 
 def features(lo, hi, m0, kappa, nev, sites) -> np.ndarray:
-    """Six O(1) inputs of the network."""
+    """Five O(1) inputs of the network: the bounds, the lattice parameters, and the wanted fraction
+    nev/sites of the spectrum (the cut follows the integrated density of states at that fraction; nev
+    alone is left out, so that a large lattice with many wanted pairs interpolates between smaller
+    lattices at the same fraction instead of extrapolating)."""
     return np.array([(lo - m0) / 8.0, (hi - m0) / 8.0, m0 - 9.0, (kappa - 0.3) / 0.2,
-                     np.log(nev / sites) / 3.0 + 2.0, np.log(nev) / 2.0 - 1.5], dtype=np.float32)
+                     np.log(nev / sites) / 3.0 + 2.0], dtype=np.float32)
+
+
+# Where the filter's step sits, in units of its transition width pi/DEGREE (in theta = arccos of the
+# window coordinate): CUT_OFFSET widths below lambda_nev, so that the wanted eigenvalues lie in the
+# steep lower tail of the damped step, where p falls by a large factor from each wanted eigenvalue to
+# the next (relative gaps in the spectrum of B = p(A) are what Lanczos resolves).  Measured on GB300
+# with the step moved over offsets 1.5, 2, 2.5, 3 (24^3 x 48, nev 100: 13.7, 12.2, 16.8, 206 s; the
+# midpoint between lambda_nev and lambda_{nev+1}: 22.5 s): 2 was the fastest, or within 2% of it, on
+# 8^4 (nev 20), 12^4 (nev 30 and 100), 16^4 (nev 50) and 24^3 x 48; near 3 a ripple of the damped step
+# meets the wanted set and the solve slows by 5-17x.  The target is 1.75 widths: within a few percent
+# of the fastest, and a quarter width further from that cliff than the prediction error allows.
+CUT_OFFSET = 1.75
 
 
 def cut_tau(ev_sorted, nev, a, b) -> float:
-    """Window coordinate of the cut between lambda_nev and lambda_{nev+1}, kept inside (-1, 1)."""
-    cut = 0.5 * (ev_sorted[nev - 1] + ev_sorted[nev])
+    """Window coordinate tau of the step for a problem whose lowest eigenvalues are ev_sorted: theta =
+    arccos((lambda_nev - c)/e) + CUT_OFFSET pi / DEGREE, tau = cos(theta), kept inside (-1, 1)."""
     c, e = 0.5 * (a + b), 0.5 * (b - a)
-    return float(np.clip((cut - c) / e, -0.999, 0.999))
+    t_nev = float(np.clip((ev_sorted[nev - 1] - c) / e, -1.0, 1.0))
+    theta = min(np.arccos(t_nev) + CUT_OFFSET * np.pi / DEGREE, np.pi)
+    return float(np.clip(np.cos(theta), -0.9999, 0.999))
 
 
 class FilterNet:
@@ -131,9 +149,10 @@ def cut_of(coeffs) -> float:
 
 
 def at_degree(coeffs, degree, device="cuda") -> np.ndarray:
-    """The network's filter at another degree: the Jackson-damped step with the same cut."""
-    if degree == len(coeffs) - 1:
-        return np.asarray(coeffs, dtype=np.float64)
+    """The Jackson-damped step of the given degree whose cut is the one the network's coefficients
+    encode (g_0).  The solver always takes this exact step, not the network's raw coefficients: the
+    wanted eigenvalues sit in the step's tail, where p is 1e-3 to 1e-5 and the raw outputs' error
+    (about 1e-3 per coefficient) would swamp it."""
     return damped_targets([cut_of(coeffs)], device, degree)[0].astype(np.float64)
 
 
@@ -147,25 +166,24 @@ def stencil_bounds(U, W, dims, m0, kappa, device="cuda"):
     return lo, hi
 
 
-def learned_filter(net: FilterNet, U, W, dims, m0, kappa, nev, device="cuda"):
-    """(coefficients, window, features) predicted for one stencil problem."""
+def learned_filter(net: FilterNet, U, W, dims, m0, kappa, nev, device="cuda", degree=DEGREE):
+    """(coefficients, window, features) predicted for one stencil problem: the damped step at the
+    network's cut (at_degree)."""
     lo, hi = stencil_bounds(U, W, dims, m0, kappa, device)
     sites = int(np.prod(dims))
     f = features(lo, hi, m0, kappa, nev, sites)
-    g = net.predict(f[None, :])[0]
+    g = at_degree(net.predict(f[None, :])[0], degree, net.device)
     return g, window(lo, hi), f
 
 
 def filter_on_context(net: FilterNet, ctx, m0, kappa, nev, sites, degree=None):
     """The learned filter for the operator of an existing context, set on that context: jtrlan_bounds
     on the context itself, network inference, jtrlan_set_filter.  Returns (coefficients, window,
-    features); the next jtrlan_solve of the context runs on B = p(A).  degree: the filter's degree
-    if not the network's own (the damped step with the predicted cut)."""
+    features); the next jtrlan_solve of the context runs on B = p(A), p the damped step at the
+    network's cut (at_degree) of the given degree (default: the network's own)."""
     lo, hi = B.jtrlan_bounds(ctx, BOUNDS_STEPS)
     f = features(lo, hi, m0, kappa, nev, sites)
-    g = net.predict(f[None, :])[0]
-    if degree:
-        g = at_degree(g, degree, net.device)
+    g = at_degree(net.predict(f[None, :])[0], degree or DEGREE, net.device)
     win = window(lo, hi)
     B.jtrlan_set_filter(ctx, g, win)
     return g, win, f

@@ -112,6 +112,7 @@ def main():
     ap.add_argument("--concurrency", type=int, default=1)
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--out", default=LF.WEIGHTS)
+    ap.add_argument("--add", default=None, help="LxLxLxL:COUNT -- run COUNT more runs on that lattice and append them")
     args = ap.parse_args()
     counts = [int(c) for c in args.runs.split(",")]
     t0 = time.perf_counter()
@@ -126,6 +127,15 @@ def main():
         json.dump(records, open(args.data, "w"))
     else:
         records = json.load(open(args.data))
+    if args.add:
+        lat, cnt = args.add.split(":")
+        dims = tuple(int(v) for v in lat.split("x"))
+        start = max(r["i"] for r in records) + 1
+        plan = [(start + k, dims) for k in range(int(cnt))]
+        records += generate(plan, tol=args.tol, concurrency=args.concurrency,
+                            log=lambda r: print(json.dumps({k: r[k] for k in ("i", "dims", "seconds", "n_matvec")}),
+                                                flush=True))
+        json.dump(records, open(args.data, "w"))
     t_data = time.perf_counter() - t0
     counts = [sum(1 for r in records if tuple(r["dims"]) == tuple(d)) for d in LATTICES]
     X, T, taus, groups = samples(records)

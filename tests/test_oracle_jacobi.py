@@ -82,3 +82,15 @@ def test_planted_wrong_rotation_sign_is_caught(monkeypatch):
     lam, Z = ns["jacobi_eigh"](T)
     assert np.abs(lam - np.linalg.eigvalsh(T)).max() < 1e-12
     assert np.abs(Z @ np.diag(lam) @ Z.T - T).max() > 1e-3
+
+
+def test_negligible_couplings_do_not_overflow():
+    """A coupling 1e-300 next to a diagonal gap of 1 makes tau^2 overflow in the textbook formula; the
+    rotation then tends to the identity (t -> 1/(2 tau)), and the result is the diagonal."""
+    import warnings
+    T = np.array([[1.0, 1e-300, 0.0], [1e-300, 2.0, 0.3], [0.0, 0.3, 5.0]])
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        lam, Z = jacobi_eigh(T)
+    assert np.abs(lam - np.linalg.eigvalsh(T)).max() < 1e-14
+    _check(T, lam, Z)
