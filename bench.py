@@ -89,9 +89,9 @@ BYTES_PER_UNIT = {"matvec": 84 * 16.0, "resid": 84 * 16.0, "gs_first": 32.0, "gs
 # SHA-256 of the source file the capture was built from: the figure is reported only while that file
 # is unchanged (roofline.traffic is null otherwise).
 NCU_TRAFFIC = {
-    "matvec": dict(bytes=687.6e6, workload="stencil_24x24x24x48", kernel="stencil_df_cheb_kernel<float2> (middle step)",
+    "matvec": dict(bytes=688.2e6, workload="stencil_24x24x24x48", kernel="stencil_df_cheb_kernel<float2> (middle step)",
                    source="paper_2001_07428_gb300/csrc/gsdf.cu",
-                   sha256="e7dd4f02ac124e32d7db1998d3d07f30b666cf80e243739e4e04334593b75b83"),
+                   sha256="1a804e49a1ede1f83a2766f468e83f21386804e53c884101c198dc922133231b"),
     "gs_step": dict(bytes=13.66e6, workload="stencil_8x8x8x8", kernel="gs_step_coop_kernel<double>",
                     source="paper_2001_07428_gb300/csrc/gs.cu",
                     sha256="25f4b188216fe6b311d90026b3e55046646e3a430ba0d7a2b9d8b809fdae98b5"),
@@ -946,16 +946,19 @@ def fp32_peak_ops(peaks=None):
 # Algorithmic work per unit of each kernel class of the learned-filter solve (units from the library's
 # jtrlan_profile work counters), with the roof that bounds it.
 #   matvec: the compensated stencil product fused with one Chebyshev step (per lattice site): 1152 real
-#     products (288 complex multiply-adds of 3x3 links by neighbour colour vectors, both halves), each an
-#     exact FMA split (2 ops), a first-order cross term (1 op), a TwoSum into the running sum (6 ops) and
-#     the error accumulation (3 ops) = 12 FP32 ops; plus the float-float recurrence epilogue (about 150
-#     ops per (site, colour), 450 per site): 14,274 FP32 ops per site, FP32-issue-bound ("alu").
+#     products (288 complex multiply-adds of 3x3 complex64 links by neighbour colour vectors, both
+#     halves) carried as biased block sums, 5 FP32 ops each (FMA into the biased sum, the exact amount
+#     added, the FMA's rounding error, two into the error sum) = 5760; the bounds of the 12 blocks per
+#     site (one per direction and colour row: 42 ops each) = 504; the rebias of 8 running sums per block
+#     (5 ops each) = 480; the biases (3 FP32 ops each, 2 per block) = 72; the start and the removal of the
+#     bias = 33; the float-float recurrence epilogue (about 150 ops per (site, colour)) = 450:
+#     7,299 FP32 ops per site, against the FP32 issue rate ("alu").
 #   gs_first, gs_dot, gs_update: per (row pair x basis column) the two (hi, lo) complex entries of V
 #     read from HBM, 32 B ("hbm").
 #   rotate: per real multiply-add of V_m Z, 2 flop FP64-equivalent; issued on the tensor cores as
 #     28 BF16 digit-pair products (56 flop), against the measured BF16 peak ("tensor").
 LEARNED_UNIT_WORK = {
-    "matvec": ("alu", 1152 * 12 + 450, "FP32 op"),
+    "matvec": ("alu", 1152 * 5 + 504 + 480 + 72 + 33 + 450, "FP32 op"),
     "gs_first": ("hbm", 32.0, "B"), "gs_dot": ("hbm", 32.0, "B"), "gs_update": ("hbm", 32.0, "B"),
     "rotate": ("tensor", 28.0, "flop"),     # x the FP64-equivalent flop count 2 n m kk of the work counter
 }

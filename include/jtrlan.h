@@ -233,9 +233,15 @@ jtrlan_status jtrlan_get_profile(jtrlan_ctx* ctx, jtrlan_profile* out);
 /* Frees everything the context owns (after synchronising its stream).  NULL is a no-op. */
 void jtrlan_destroy(jtrlan_ctx* ctx);
 
-/* y = p(A) x with the filter of params (filter_degree > 0) and the FP32 operator of a JTRLAN_MIXED
- * context: x, y DEVICE complex64 vectors of n entries (distinct).  Enqueued on the context stream.
- * Errors: JTRLAN_EINVAL (null, or no filter), JTRLAN_ECUDA. */
+/* y = p(A) x by the Chebyshev recurrence of the context's filter (window filter_lo..filter_hi):
+ *   - a JTRLAN_MIXED context with an FP32-phase filter (filter_degree > 0): that filter with the FP32
+ *     operator; x, y DEVICE complex64 vectors of n entries;
+ *   - otherwise a context with a certifying filter (filter_final_degree > 0, or jtrlan_set_filter):
+ *     that filter with the product the solve uses in its certifying phase (FP64, or on the stencil of
+ *     the mixed forms the compensated-FP32 product fused with a float-float recurrence step); x, y
+ *     DEVICE complex128 vectors of n entries.
+ * x and y distinct.  Enqueued on the context stream; uses the context's filter buffers (no call on
+ * the same context may overlap it).  Errors: JTRLAN_EINVAL (null, or no filter), JTRLAN_ECUDA. */
 jtrlan_status jtrlan_apply_filter(jtrlan_ctx* ctx, const void* x, void* y);
 
 /* Spectral bounds for a filter window (the paper has no counterpart): `steps` Lanczos steps of

@@ -564,52 +564,52 @@ jtrlan_status filter_apply(jtrlan_ctx* c, Phase& ph, const void* v, void* y, dou
   return JTRLAN_OK;
 }
 
-// The certifying phase's product y = p(A) v_j in FP64 vectors: FP64 products, or compensated-FP32
-// products on (hi, lo) copies that each recurrence step leaves beside its FP64 vector (stencil
-// double-float phase); alpha partials of conj(v_j) y in ph.alpha_part (cheb_blocks(n)).
-jtrlan_status filter_apply_cert(jtrlan_ctx* c, Phase& ph, int j) {
+// The certifying phase's product y = p(A) v in FP64 vectors, v given in FP64 (v64) and, for the
+// stencil double-float phase, as (hi, lo) pairs (vdf): there each recurrence step is fused into the
+// compensated-FP32 product (float-float recurrence, (hi, lo) vectors between steps); otherwise FP64
+// products and FP64 recurrence steps.  Alpha partials of conj(v) y in ph.alpha_part (cheb_blocks(n)).
+jtrlan_status filter_apply_cert_io(jtrlan_ctx* c, Phase& ph, const void* v64, const void* vdf, void* y) {
   cudaStream_t s = c->stream;
   const int64_t n = c->n;
   const int d = (int)ph.fcoef.size() - 1;
   const double* g = ph.fcoef.data();
-  if (ph.dfmv) {   // stencil: each recurrence step fused into the compensated-FP32 product (float-float)
+  if (ph.dfmv) {
     void* acc = ph.fbuf[0];
     void* B[2] = {ph.fbuf[1], ph.fbuf[2]};
-    const void* vj = col(ph.V, n, j, ph.cs);
     const OpDev& o = ph.opdf;
-    LAUNCH(K_MATVEC, launch_matvec_df_cheb(o, vj, nullptr, B[1], acc, vj, ph.y, ph.alpha_part, o.kappa, o.m0, c->fc,
+    LAUNCH(K_MATVEC, launch_matvec_df_cheb(o, vdf, nullptr, B[1], acc, vdf, y, ph.alpha_part, o.kappa, o.m0, c->fc,
                                            1.0 / c->fe, g[1], g[0], 1, d == 1, s));
     for (int k = 2; k <= d; ++k)
-      LAUNCH(K_MATVEC, launch_matvec_df_cheb(o, B[(k - 1) & 1], k == 2 ? vj : B[k & 1], B[k & 1], acc, vj, ph.y,
+      LAUNCH(K_MATVEC, launch_matvec_df_cheb(o, B[(k - 1) & 1], k == 2 ? vdf : B[k & 1], B[k & 1], acc, vdf, y,
                                              ph.alpha_part, o.kappa, o.m0, c->fc, 2.0 / c->fe, g[k], 0.0, 0, k == d,
                                              s));
     return JTRLAN_OK;
   }
   void* ax = ph.fbuf[0];
   void* B[2] = {ph.fbuf[1], ph.fbuf[2]};
-  void* sp = ph.fbuf[3];
-  const void* v = ph.df ? ph.x : col(ph.V, n, j, ph.cs);   // v_j in FP64
-  auto product = [&](const void* t64, const void* t4) -> jtrlan_status {
-    if (ph.dfmv)
-      LAUNCH(K_MATVEC, launch_matvec_df(ph.opdf, t4, ax, nullptr, s));
-    else
-      LAUNCH(K_MATVEC, launch_matvec<double>(ph.op, (const double2*)t64, (double2*)ax, MV_PLAIN, nullptr, nullptr,
-                                             nullptr, 0, 0, nullptr, s));
+  const void* v = v64;
+  auto product = [&](const void* t64) -> jtrlan_status {
+    LAUNCH(K_MATVEC, launch_matvec<double>(ph.op, (const double2*)t64, (double2*)ax, MV_PLAIN, nullptr, nullptr,
+                                           nullptr, 0, 0, nullptr, s));
     return JTRLAN_OK;
   };
-  JT_TRY(product(v, col(ph.V, n, j, ph.cs)));
-  LAUNCH(K_FILTER, launch_cheb_step<double>(ax, v, nullptr, B[1], ph.y, v, n, c->fc, 1.0 / c->fe, 0.0, g[1], g[0], 1,
-                                            d == 1 ? ph.alpha_part : nullptr, (ph.dfmv && d > 1) ? sp : nullptr, s));
+  JT_TRY(product(v));
+  LAUNCH(K_FILTER, launch_cheb_step<double>(ax, v, nullptr, B[1], y, v, n, c->fc, 1.0 / c->fe, 0.0, g[1], g[0], 1,
+                                            d == 1 ? ph.alpha_part : nullptr, nullptr, s));
   for (int k = 2; k <= d; ++k) {
     const void* tcur = B[(k - 1) & 1];
     const void* tprev = k == 2 ? v : B[k & 1];
     void* tnext = B[k & 1];
-    JT_TRY(product(tcur, sp));
-    LAUNCH(K_FILTER, launch_cheb_step<double>(ax, tcur, tprev, tnext, ph.y, v, n, c->fc, 2.0 / c->fe, 1.0, g[k], 0.0,
-                                              0, k == d ? ph.alpha_part : nullptr, (ph.dfmv && k < d) ? sp : nullptr,
-                                              s));
+    JT_TRY(product(tcur));
+    LAUNCH(K_FILTER, launch_cheb_step<double>(ax, tcur, tprev, tnext, y, v, n, c->fc, 2.0 / c->fe, 1.0, g[k], 0.0,
+                                              0, k == d ? ph.alpha_part : nullptr, nullptr, s));
   }
   return JTRLAN_OK;
+}
+
+jtrlan_status filter_apply_cert(jtrlan_ctx* c, Phase& ph, int j) {
+  const void* vj = col(ph.V, c->n, j, ph.cs);
+  return filter_apply_cert_io(c, ph, ph.df ? ph.x : vj, vj, ph.y);   // v_j in FP64: ph.x beside a (hi, lo) basis
 }
 
 // Rayleigh quotient lam_out = x^H A x and residual res_out = ||A x - lam x|| of one FP64 column
@@ -1210,9 +1210,15 @@ jtrlan_status jtrlan_get_profile(jtrlan_ctx* c, jtrlan_profile* out) {
 
 jtrlan_status jtrlan_apply_filter(jtrlan_ctx* c, const void* x, void* y) {
   if (!c || !x || !y) return fail(JTRLAN_EINVAL, "null argument");
-  if (!c->p32.filtered) return fail(JTRLAN_EINVAL, "the context has no filter");
   cudaStream_t s = c->stream;
-  JT_TRY(filter_apply<float>(c, c->p32, x, y, nullptr));
+  if (c->p32.filtered) {
+    JT_TRY(filter_apply<float>(c, c->p32, x, y, nullptr));
+    return JTRLAN_OK;
+  }
+  Phase& ph = c->mixed ? c->pdf : c->p64;
+  if (!ph.certify) return fail(JTRLAN_EINVAL, "the context has no filter");
+  if (ph.dfmv) LAUNCH(K_RESID, launch_df_from_fp64(x, ph.fbuf[3], c->n, s));
+  JT_TRY(filter_apply_cert_io(c, ph, x, ph.fbuf[3], y));
   return JTRLAN_OK;
 }
 

@@ -756,12 +756,16 @@ rotate_df_kernel(const float4* __restrict__ V, int64_t n, int m, const double* _
 // ------------------------------------------------------------------ double-float stencil matvec
 // y (FP64) = A x for x given as (hi, lo) pairs (a column of the mixed basis), links given as (hi, lo)
 // pairs in structure-of-arrays layout L[(mu*9 + e)*V + s] (float4 per complex).  One thread per
-// (site, colour) as in the FP32 kernel; every complex multiply-add is four df_acc, so the result
-// has FP64-level accuracy while the arithmetic runs on the FP32 pipes.  With `part` non-null the
-// block partials of x^H y (FP64) are written for alpha.
+// (site, colour) as in the FP32 kernel.  The product of the Lanczos steps and of the certifying
+// residuals and Rayleigh quotients (stencil_df_kernel) makes every complex multiply-add four df_acc
+// (Dot2), so its result has FP64-level accuracy while the arithmetic runs on the FP32 pipes; the
+// filter's fused Chebyshev steps (stencil_df_cheb_kernel) carry the sums as biased blocks instead.
+// With `part` non-null the block partials of x^H y (FP64) are written for alpha.
 constexpr int kDfSites = 64;
 constexpr int kDfMinBlocks = 4;   // 4 x 192 threads per SM (measured best of 2..6 at 16^4)
 
+// Dot2 form: every product split exactly and added by TwoSum (11 FP32 operations with a complex64
+// link, 12 with a (hi, lo) link).
 __device__ __forceinline__ void cdf_acc(float* s, float* e, float4 a, float4 b) {   // (re, im) += a * b
   df_acc(s[0], e[0], a.x, a.z, b.x, b.z);
   df_sub(s[0], e[0], a.y, a.w, b.y, b.w);
@@ -787,8 +791,82 @@ __device__ __forceinline__ void cdf_accc(float* s, float* e, float2 a, float4 b)
   df_acc_xa(s[1], e[1], a.x, b.y, b.w);
   df_acc_xa(s[1], e[1], -a.y, b.x, b.z);
 }
+// ------------------------------------------------------------------ block sums at a fixed bias
+// The hopping sum of one direction mu is 12 complex products per colour row whose magnitudes are
+// known before they are added (sum |a| |bh|, from the high parts of the operands).  Such sums can be
+// carried at a fixed bias: S = 1.5 sigma + (sum so far), sigma a power of two >= 2.125 times the bound
+// of the sum, keeps S inside [sigma, 2 sigma).  The FMA t = fl(S + a bh) then needs no TwoSum: t - S
+// is exactly the amount added (both lie in one binade, Sterbenz), and a bh minus that amount -- the
+// FMA's rounding error, at most half an ulp of sigma -- goes, rounded once, into the error sum e
+// together with a bl.  5 FP32 operations a product (6 with a (hi, lo) link) against 11 (12) for the
+// Dot2 form.  The bound grows direction by direction; before each direction S moves to the bias of
+// the grown bound (rebias: exact up to the part it hands to e), and at the end S - 1.5 sigma is the
+// exact high part.  The error sum now collects terms of the size of an ulp of sigma rather than of the
+// partial sums, so the result is about 16 times less accurate than Dot2: an exact emulation of the
+// sequence (fractions) over 300 random 48-term sums gave at most 2^-40.8 of sum |a| |bh|, against
+// 2^-44.8 for the Dot2 form.  The filter's Chebyshev steps use it (their products only shape the
+// Krylov space; every pair is accepted on A's residual, computed with the Dot2 form).
+
+// 1.5 sigma for the smallest power of two sigma >= 2.125 bound, with sigma in [2^-100, 2^126] (a bound
+// below 2^-100 only ever meets products that small; one above 2^125 does not occur for the
+// normalised vectors of the method).
+__device__ __forceinline__ float bias_of(float bound) {
+  const float v = fminf(fmaxf(2.125f * bound, 7.8886091e-31f), 8.5070592e+37f);
+  const uint32_t p2 = (__float_as_uint(v) + 0x007fffffu) & 0x7f800000u;   // next power of two >= v
+  return __uint_as_float(p2 | 0x00400000u);                               // 1.5 * sigma
+}
+// (S, e) += a * (bh + bl), a exact in FP32 (a complex64 link)
+__device__ __forceinline__ void bias_acc(float& S, float& e, float a, float bh, float bl) {
+  const float t = __fmaf_rn(a, bh, S);
+  e = __fmaf_rn(a, bl, __fadd_rn(e, __fmaf_rn(a, bh, -__fsub_rn(t, S))));
+  S = t;
+}
+// (S, e) += (ah + al) * (bh + bl): the same with al * bh in the error sum
+__device__ __forceinline__ void bias_acc(float& S, float& e, float ah, float al, float bh, float bl) {
+  const float t = __fmaf_rn(ah, bh, S);
+  e = __fmaf_rn(al, bh, __fmaf_rn(ah, bl, __fadd_rn(e, __fmaf_rn(ah, bh, -__fsub_rn(t, S)))));
+  S = t;
+}
+// (re, im) += a * b and += conj(a) * b for b = (hi.re, hi.im, lo.re, lo.im)
+__device__ __forceinline__ void cbias_acc(float* S, float* e, float2 a, float4 b) {
+  bias_acc(S[0], e[0], a.x, b.x, b.z);
+  bias_acc(S[0], e[0], -a.y, b.y, b.w);
+  bias_acc(S[1], e[1], a.x, b.y, b.w);
+  bias_acc(S[1], e[1], a.y, b.x, b.z);
+}
+__device__ __forceinline__ void cbias_accc(float* S, float* e, float2 a, float4 b) {
+  bias_acc(S[0], e[0], a.x, b.x, b.z);
+  bias_acc(S[0], e[0], a.y, b.y, b.w);
+  bias_acc(S[1], e[1], a.x, b.y, b.w);
+  bias_acc(S[1], e[1], -a.y, b.x, b.z);
+}
+__device__ __forceinline__ void cbias_acc(float* S, float* e, float4 a, float4 b) {
+  bias_acc(S[0], e[0], a.x, a.z, b.x, b.z);
+  bias_acc(S[0], e[0], -a.y, -a.w, b.y, b.w);
+  bias_acc(S[1], e[1], a.x, a.z, b.y, b.w);
+  bias_acc(S[1], e[1], a.y, a.w, b.x, b.z);
+}
+__device__ __forceinline__ void cbias_accc(float* S, float* e, float4 a, float4 b) {
+  bias_acc(S[0], e[0], a.x, a.z, b.x, b.z);
+  bias_acc(S[0], e[0], a.y, a.w, b.y, b.w);
+  bias_acc(S[1], e[1], a.x, a.z, b.y, b.w);
+  bias_acc(S[1], e[1], -a.y, -a.w, b.x, b.z);
+}
 __device__ __forceinline__ float4 cneg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
 __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+// |re| + |im| of the high part
+__device__ __forceinline__ float l1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__device__ __forceinline__ float l1(float4 a) { return fabsf(a.x) + fabsf(a.y); }
+
+// Moves S from bias bo = 1.5 sigma_o to bn = 1.5 sigma_n (sigma_n >= sigma_o, |S - bo| < sigma_o / 2):
+// S - bo is exact (Sterbenz), adding bn rounds to the new binade's ulp, and what that rounding
+// dropped, (S - bo) - (t - bn), is exact and goes into e.  With sigma_n = sigma_o nothing moves.
+__device__ __forceinline__ void rebias(float& S, float& e, float bo, float bn) {
+  const float d = __fsub_rn(S, bo);
+  const float t = __fadd_rn(d, bn);
+  e = __fadd_rn(e, __fsub_rn(d, __fsub_rn(t, bn)));
+  S = t;
+}
 
 // The hopping sums of site s, colour a, in compensated FP32: (ys1, ye1) and (ys2, ye2) for the U
 // terms of y1 and y2, (ws1, we1) and (ws2, we2) for the W terms (kappa not yet applied).
@@ -799,8 +877,9 @@ struct DfSums {
 // A link as stored: a (hi, lo) float4 pair, or a float2 exact in FP32 (complex64 links), for which
 // the products take the shorter exact-multiplier form.
 
+// The sums in the Dot2 form (the certifying product: residuals and Rayleigh quotients).
 template <typename LinkT>
-__device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* __restrict__ x, int s, int a,
+__device__ __forceinline__ void stencil_df_sums_dot2(const OpDev& op, const float4* __restrict__ x, int s, int a,
                                                 DfSums& r) {
   const int vol = (int)op.vol;
   const int64_t h = op.h;
@@ -850,6 +929,99 @@ __device__ __forceinline__ void stencil_df_sums(const OpDev& op, const float4* _
   }
 }
 
+// The sums as biased blocks, one per direction (the Chebyshev steps of the filter).
+template <typename LinkT>
+__device__ __forceinline__ void stencil_df_sums_biased(const OpDev& op, const float4* __restrict__ x, int s, int a,
+                                                DfSums& r) {
+  const int vol = (int)op.vol;
+  const int64_t h = op.h;
+  const LinkT* U = (const LinkT*)op.U;
+  const LinkT* W = (const LinkT*)op.W;
+  const float4* x1 = x;
+  const float4* x2 = x + h;
+  // running sums held at a bias (S) with their error sums (e); one bound for the two U sums and one
+  // for the two W sums (sum |a| |bh| over both, over the blocks so far: at most twice either's own)
+  float ou = bias_of(0.f), ow = ou;
+  float bu = 0.f, bw = 0.f;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    r.ys1[c] = r.ys2[c] = r.ws1[c] = r.ws2[c] = ou;
+    r.ye1[c] = r.ye2[c] = r.we1[c] = r.we2[c] = 0.f;
+  }
+  const int d0 = op.dims[0], d1 = op.dims[1], d2 = op.dims[2], d3 = op.dims[3];
+  // the site's coordinates, once (x fastest)
+  const int r1 = s / d0, r2 = r1 / d1;
+  const int x0 = s - r1 * d0, x1c = r1 - r2 * d1, x2c = r2 % d2, x3c = r2 / d2;
+  int stride = 1;
+  // the direction loop stays rolled: unrolled, its 4 x 3 x 8 compensated products overflowed the
+  // instruction cache (ncu: "no instruction" stalls as frequent as memory stalls); extents and
+  // coordinates are selected in registers, not indexed
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    const int L = mu == 0 ? d0 : mu == 1 ? d1 : mu == 2 ? d2 : d3;
+    const int c = mu == 0 ? x0 : mu == 1 ? x1c : mu == 2 ? x2c : x3c;
+    const int sp = (c == L - 1) ? s - (L - 1) * stride : s + stride;
+    const int sm = (c == 0) ? s + (L - 1) * stride : s - stride;
+    stride *= L;
+    const LinkT* Um = U + (int64_t)mu * 9 * vol;
+    const LinkT* Wm = W + (int64_t)mu * 9 * vol;
+    // the block's bound first (high parts only), then its products: the operands are read twice
+    // (the second time from L1) rather than held, which would spill
+    const float2* x1h = reinterpret_cast<const float2*>(x1);
+    const float2* x2h = reinterpret_cast<const float2*>(x2);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float nuf = l1(Um[(a * 3 + b) * vol + s]), nub = l1(Um[(b * 3 + a) * vol + sm]);
+      const float nwf = l1(Wm[(a * 3 + b) * vol + s]), nwb = l1(Wm[(b * 3 + a) * vol + sm]);
+      const float np = l1(x1h[2 * (3 * sp + b)]) + l1(x2h[2 * (3 * sp + b)]);
+      const float nm = l1(x1h[2 * (3 * sm + b)]) + l1(x2h[2 * (3 * sm + b)]);
+      bu = fmaf(nuf, np, fmaf(nub, nm, bu));
+      bw = fmaf(nwf, np, fmaf(nwb, nm, bw));
+    }
+    {
+      const float nu = bias_of(bu), nw = bias_of(bw);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        rebias(r.ys1[q], r.ye1[q], ou, nu);
+        rebias(r.ys2[q], r.ye2[q], ou, nu);
+        rebias(r.ws1[q], r.we1[q], ow, nw);
+        rebias(r.ws2[q], r.we2[q], ow, nw);
+      }
+      ou = nu; ow = nw;
+    }
+    auto products = [&](int b) {
+      const float4 p1 = x1[3 * sp + b], p2 = x2[3 * sp + b];
+      const float4 m1 = x1[3 * sm + b], m2 = x2[3 * sm + b];
+      const LinkT uf = Um[(a * 3 + b) * vol + s];    // U(s)_{ab}
+      const LinkT ub = Um[(b * 3 + a) * vol + sm];   // U(s-mu)_{ba}
+      const LinkT wf = Wm[(a * 3 + b) * vol + s];    // W(s)_{ab}
+      const LinkT wb = Wm[(b * 3 + a) * vol + sm];   // W(s-mu)_{ba}
+      cbias_acc(r.ys1, r.ye1, uf, p1);           // U(s) x1(s+mu)
+      cbias_accc(r.ys1, r.ye1, ub, m1);          // U(s-mu)^H x1(s-mu)
+      cbias_accc(r.ys2, r.ye2, uf, p2);          // U(s)^* x2(s+mu)
+      cbias_acc(r.ys2, r.ye2, ub, m2);           // U(s-mu)^T x2(s-mu)
+      cbias_acc(r.ws1, r.we1, wf, p2);           // W(s) x2(s+mu)
+      cbias_acc(r.ws1, r.we1, cneg(wb), m2);     // -W(s-mu)^T x2(s-mu)
+      cbias_accc(r.ws2, r.we2, cneg(wf), p1);    // -W(s)^* x1(s+mu)
+      cbias_accc(r.ws2, r.we2, wb, m1);          // +W(s-mu)^H x1(s-mu)
+    };
+    if constexpr (sizeof(LinkT) == sizeof(float2)) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) products(b);
+    } else {   // (hi, lo) links: unrolled, the operands of the three b spill at 80 registers
+#pragma unroll 1
+      for (int b = 0; b < 3; ++b) products(b);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {   // the high parts without their bias (exact)
+    r.ys1[q] = __fsub_rn(r.ys1[q], ou);
+    r.ys2[q] = __fsub_rn(r.ys2[q], ou);
+    r.ws1[q] = __fsub_rn(r.ws1[q], ow);
+    r.ws2[q] = __fsub_rn(r.ws2[q], ow);
+  }
+}
+
 template <typename LinkT>
 __global__ void __launch_bounds__(3 * kDfSites, kDfMinBlocks)
 stencil_df_kernel(OpDev op, const float4* __restrict__ x, double2* __restrict__ Y, double* __restrict__ part) {
@@ -861,7 +1033,7 @@ stencil_df_kernel(OpDev op, const float4* __restrict__ x, double2* __restrict__ 
   double c0 = 0.0, c1 = 0.0;
   if (s < vol) {
     DfSums r;
-    stencil_df_sums<LinkT>(op, x, s, a, r);
+    stencil_df_sums_dot2<LinkT>(op, x, s, a, r);
     const int64_t e1 = 3 * (int64_t)s + a;
     const double2 xa = join(x[e1]), xb = join(x[h + e1]);
     const double kap = op.kappa, m0 = op.m0;
@@ -921,8 +1093,10 @@ struct ChebConsts {
 // (x = t_k, the current recurrence vector, as (hi, lo)):
 //   t_next = sc (A t - c t) - t_prev     (t_prev omitted when null)
 //   acc    = g0 v + g t_next (init)   or   acc += g t_next
-// all in float-float arithmetic on the FP32 pipe; t_next and acc are stored as (hi, lo) float4, so
-// t_next feeds the next product directly.  On the last step acc goes out in FP64 to y, with the
+// all in float-float arithmetic on the FP32 pipe, the hopping sums as biased blocks (one per direction;
+// 5 FP32 operations a product); t_next and acc are stored as (hi, lo) float4, so t_next feeds the next
+// product directly.  On 24^3 x 48 this took a launch from 322 to about 255 us (the step from 12.2 to
+// 10.5 s, the same products and restarts); on the last step acc goes out in FP64 to y, with the
 // per-block partials of conj(v) y (the alpha of Algorithm 2).  t_next may alias t_prev (the same
 // thread reads an entry before writing it); neighbours are read from x only.
 template <typename LinkT>
@@ -938,7 +1112,7 @@ stencil_df_cheb_kernel(OpDev op, const float4* __restrict__ x, const float4* t_p
   double c0 = 0.0, c1 = 0.0;
   if (s < vol) {
     DfSums r;
-    stencil_df_sums<LinkT>(op, x, s, a, r);
+    stencil_df_sums_biased<LinkT>(op, x, s, a, r);
     const int64_t e1 = 3 * (int64_t)s + a;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {

@@ -56,6 +56,7 @@ class JTRLan:
         self._keep_v1 = keep[-1] if v1 is not None else None
         prec = {"fp64": B.JTRLAN_FP64, "mixed": B.JTRLAN_MIXED, "mixed_reorth": B.JTRLAN_MIXED_REORTH}[precision]
         self.mixed = prec != B.JTRLAN_FP64
+        self.fp32_filter = prec == B.JTRLAN_MIXED and filter_coeffs is not None and len(filter_coeffs) > 1
         prm = B.params(nev, m, mwin, tol, which=w, precision=prec, max_restarts=max_restarts,
                        gs_max_passes=gs_max_passes, v1_ptr=v1p, check_jsym=int(check_jsym),
                        profile=int(profile), filter_coeffs=filter_coeffs, filter_window=filter_window,
@@ -90,8 +91,11 @@ class JTRLan:
         return B.jtrlan_get_profile(self.ctx)
 
     def apply_filter(self, x: torch.Tensor) -> torch.Tensor:
-        """y = p(A) x with the context's filter and FP32 operator (complex64)."""
-        x = _dev(x, self.device).to(torch.complex64)
+        """y = p(A) x with the context's filter: the FP32-phase filter and FP32 operator (complex64) where
+        the context has one, else the certifying filter with the solve's own product (complex128)."""
+        x = _dev(x, self.device)
+        if self.fp32_filter:
+            x = x.to(torch.complex64)
         y = torch.empty_like(x)
         B.jtrlan_apply_filter(self.ctx, x.data_ptr(), y.data_ptr())
         return y

@@ -67,6 +67,46 @@ def test_filter_apply_matches_oracle(kind, degree):
     s.close()
 
 
+# ----------------------------------------------------------------------------- certifying filter
+# The certifying phase's p(A) x through jtrlan_apply_filter, against the oracle's FP64 recurrence on
+# the same links.  Tolerances from the arithmetic, relative to max|p(A) x|:
+#   * mixed_reorth stencil: each Chebyshev step fused into the compensated-FP32 product whose sums are
+#     carried at a fixed bias per direction, about 2^-40.8 of sum |a| |x| a product (an exact
+#     emulation of the sequence: the worst of 300 random 48-term sums); over d steps of the recurrence
+#     the errors add up to about d times that, held to 10 d 2^-40.8 (3.2e-10 at d = 64; the FP32 case
+#     above is held to 5 d u the same way);
+#   * FP64: FP64 products and recurrence, 10 d 2^-52.
+# Lattices (3, 5, 2, 7) (210 sites: four 64-site blocks, the last ragged) and 8^4 (64 blocks).
+@pytest.mark.parametrize("dims,links,degree,precision", [
+    ((3, 5, 2, 7), "c64", 1, "mixed_reorth"), ((3, 5, 2, 7), "c64", 64, "mixed_reorth"),
+    ((3, 5, 2, 7), "c128", 64, "mixed_reorth"), ((8, 8, 8, 8), "c64", 64, "mixed_reorth"),
+    ((8, 8, 8, 8), "c128", 17, "mixed_reorth"), ((3, 5, 2, 7), "c128", 64, "fp64")])
+def test_certifying_filter_product_matches_oracle(dims, links, degree, precision):
+    U, W = inputs.stencil_links(dims, 7)
+    if links == "c64":                                   # the kernels read these links exactly
+        U = U.astype(np.complex64).astype(np.complex128)
+        W = W.astype(np.complex64).astype(np.complex128)
+    mv = lambda x: jsym.stencil_matvec(U, W, dims, 8.5, 0.3, x)
+    n = 6 * int(np.prod(dims))
+    probe = _solver(kind="stencil", dims=dims, m0=8.5, kappa=0.3, U=U, W=W, nev=2, m=40, mwin=4, tol=1e-8,
+                    precision=precision, links_dtype=links)
+    lo, hi = probe.bounds(30)
+    probe.close()
+    win = (lo - 0.05 * (hi - lo), hi + 0.05 * (hi - lo))
+    rng = np.random.default_rng(100 + degree)
+    g = rng.standard_normal(degree + 1) / np.sqrt(degree + 1)
+    s = _solver(kind="stencil", dims=dims, m0=8.5, kappa=0.3, U=U, W=W, nev=2, m=16, mwin=4, tol=1e-8,
+                precision=precision, links_dtype=links, filter_final_coeffs=g, filter_window=win)
+    x = inputs.random_vector(n, 11)
+    y = s.apply_filter(torch.from_numpy(x))
+    assert y.dtype == torch.complex128
+    y = y.cpu().numpy()
+    ref = flt.apply_poly(mv, x, g, *win)
+    u = 2.0 ** -40.8 if precision == "mixed_reorth" else 2.0 ** -52
+    assert np.abs(y - ref).max() < 10 * degree * u * np.abs(ref).max()
+    s.close()
+
+
 # ----------------------------------------------------------------------------- filtered solve
 @pytest.mark.parametrize("kind", ["dense", "stencil"])
 def test_filtered_solve_matches_unfiltered_oracle(kind):
