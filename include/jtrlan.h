@@ -92,6 +92,9 @@ typedef struct {
  *       digit splitting with FP32 accumulation in tensor memory when m <= 320 and rotate_simt is 0,
  *       else on the CUDA cores).  The vector y being orthogonalised, alpha/beta, the norms and the
  *       sqrt(2) test, the Ritz solve, the rotated Ritz vectors and the true residuals are FP64.
+ *       Inside a certifying filter's Chebyshev steps on the stencil the hopping sums are carried as
+ *       biased block sums instead of by TwoSum (about 2^-41 of sum |a| |x| against 2^-45): those
+ *       products only shape the Krylov space, and every pair is still accepted on A's residual.
  *     JTRLAN_MIXED -- an FP32 phase (matvec, Gram-Schmidt and rotation in FP32; alpha/beta, Ritz
  *       solve and residual norms in FP64) run to max(tol, 1e-5 max|t|), then the JTRLAN_MIXED_REORTH
  *       solve started from the normalised sum of the FP32 Ritz vectors, run to tol.
