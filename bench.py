@@ -91,7 +91,7 @@ BYTES_PER_UNIT = {"matvec": 84 * 16.0, "resid": 84 * 16.0, "gs_first": 32.0, "gs
 NCU_TRAFFIC = {
     "matvec": dict(bytes=688.2e6, workload="stencil_24x24x24x48", kernel="stencil_df_cheb_kernel<float2> (middle step)",
                    source="paper_2001_07428_gb300/csrc/gsdf.cu",
-                   sha256="1a804e49a1ede1f83a2766f468e83f21386804e53c884101c198dc922133231b"),
+                   sha256="f57efe4d702152935a4c602a1878b2d051606c3f149bf54843bd0f03d7e79d1e"),
     "gs_step": dict(bytes=13.66e6, workload="stencil_8x8x8x8", kernel="gs_step_coop_kernel<double>",
                     source="paper_2001_07428_gb300/csrc/gs.cu",
                     sha256="25f4b188216fe6b311d90026b3e55046646e3a430ba0d7a2b9d8b809fdae98b5"),

@@ -280,12 +280,15 @@ __global__ void __launch_bounds__(kThreads, kDotMinBlocks) gsdf_dot_kernel(GSArg
 }
 
 // The update's coefficients in shared memory, classified once per launch (every block alike):
-// column i is "large" when some component of c_v or c_w exceeds thr = 2^-27 ||y|| / ((j+1)(j+4)).
+// column i is "large" when some component of c_v or c_w exceeds thr = 2^-23 ||y|| / ((j+1)(j+4)).
 // Large columns are applied in compensated FP32 from their (hi, lo) splits scf[2i], scf[2i+1]; the
 // others enter one plain FP32 sum through csm[i] = (c_v.re, c_v.im, c_w.re, c_w.im) rounded to FP32
 // (zero for a large column), with the hi parts of V.  Each term of that sum is off by at most
 // (j + 4) 2^-24 of |v c| (product, the dropped lo parts, the recursive sum), so the whole plain part
-// errs by at most (j+4) 2^-24 sum_i |c_i| <= 2^-51 ||y||: below the compensated arithmetic's own error.
+// errs by at most (j+4) 2^-24 sum_i |c_i| <= 2^-47 ||y||, the level of the compensated dots' own
+// error.  (With 2^-27, a 2^-51 bound, the rounding-size coefficients of the filtered phase lay just
+// above the threshold once the filter's products carried their sums at about 2^-41, and most columns
+// took the compensated path: 1.10 against 0.67 ms an update at 24^3 x 48.)
 // In a Lanczos step nearly every coefficient is of rounding size (exactly, only beta_{j-1} and, after
 // a restart, the arrow couplings are not), so the update costs about one read of V instead of 16
 // compensated products per row pair and column.
@@ -296,7 +299,7 @@ struct UpdCoef {
 };
 
 __device__ __forceinline__ void classify_coefs(const coef4* coef, int j, double ynorm, UpdCoef u) {
-  const double thr = ldexp(ynorm, -27) / ((double)(j + 1) * (double)(j + 4));
+  const double thr = ldexp(ynorm, -23) / ((double)(j + 1) * (double)(j + 4));
   for (int i = threadIdx.x; i <= j; i += kThreads) {
     const coef4 c = coef[i];
     u.scf[2 * i] = split(make_double2(c.vr, c.vi));
