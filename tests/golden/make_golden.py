@@ -2,12 +2,15 @@
 
     python tests/golden/make_golden.py [WORKLOAD ...]      (default: stencil_8x8x8x8)
 
-stencil_16x16x16x16 (n = 393,216, nev 50, m 120) takes about two hours of one core.
-
 Each file records the seeded workload it came from and the oracle's nev smallest
-eigenvalues (Algorithm 1 run to tol = 1e-12 on ||A x - lambda x||, ||x|| = 1), so that
-GPU parity tests at full size need not rerun the (slow) oracle.  Nothing here touches
-the CUDA library.
+eigenvalues (Algorithm 1 run to tol on ||A x - lambda x||, ||x|| = 1), so that GPU parity
+tests at full size need not rerun the (slow) oracle.  Nothing here touches the CUDA library.
+
+tol is 1e-12 for stencil_8x8x8x8, which also records the same solve at 1e-8 (its counts scale
+the benchmark's CPU sample).  For stencil_16x16x16x16 (n = 393,216, nev 50, m 120) it is 1e-10:
+FP64 Lanczos there attains residuals of only about u ||A|| sqrt(n) ~ 1e-12, and a 1e-12 run had
+not finished after 6.4 hours of one core.  A residual r bounds each eigenvalue's error by r
+(and by r^2 / gap), so 1e-10 still pins the eigenvalues well inside a 1e-10 relative comparison.
 """
 import json
 import os
@@ -24,28 +27,43 @@ from oracle import trlan_jsym as tj  # noqa: E402
 from paper_2001_07428_gb300 import inputs  # noqa: E402
 
 
-def stencil_golden(name, tol=1e-12):
+TOL = {"stencil_8x8x8x8": 1e-12, "stencil_16x16x16x16": 1e-10}
+WITH_1E8 = {"stencil_8x8x8x8"}
+
+
+def stencil_golden(name):
+    tol = TOL[name]
     w = inputs.WORKLOADS[name]
     dims = w["dims"]
     U, W = inputs.stencil_links(dims, w["seed"])
     n = 6 * inputs.lattice_volume(dims)
     mv = lambda x: jsym.stencil_matvec(U, W, dims, w["m0"], w["kappa"], x)
     t0 = time.time()
-    out = tj.trlan_jsym(mv, n, w["nev"], w["m"], w["mwin"], tol)
+    phases = [0]
+
+    def progress(V, T, k, m):          # one line per Lanczos phase (outer iteration), to stderr
+        phases[0] += 1
+        print(f"{name}: outer iteration {phases[0]}, {time.time() - t0:.0f} s", file=sys.stderr, flush=True)
+
+    out = tj.trlan_jsym(mv, n, w["nev"], w["m"], w["mwin"], tol, on_lanczos=progress)
     rec = dict(workload=name, params=dict(w, dims=list(dims)), tol=tol,
                evals=[float(v) for v in out["evals"]], res=[float(v) for v in out["res"]],
                n_matvec=out["n_matvec"], n_restarts=out["n_restarts"],
                oracle_seconds=round(time.time() - t0, 1))
     # the same solve at the benchmark tolerance 1e-8: its outer-iteration count scales the
     # benchmark's bounded CPU-oracle sample to a whole solve
-    t0 = time.time()
-    out8 = tj.trlan_jsym(mv, n, w["nev"], w["m"], w["mwin"], 1e-8)
-    rec["tol_1e-8"] = dict(n_matvec=out8["n_matvec"], n_restarts=out8["n_restarts"],
-                           n_resid_matvec=out8["n_resid_matvec"],
-                           evals=[float(v) for v in out8["evals"]], oracle_seconds=round(time.time() - t0, 1))
+    if name in WITH_1E8:
+        rec["tol_1e-8"] = tol8_record(mv, n, w)
     with open(os.path.join(HERE, f"{name}.json"), "w") as f:
         json.dump(rec, f, indent=1)
     print(name, rec["n_matvec"], rec["n_restarts"], rec["oracle_seconds"])
+
+
+def tol8_record(mv, n, w):
+    t0 = time.time()
+    out8 = tj.trlan_jsym(mv, n, w["nev"], w["m"], w["mwin"], 1e-8)
+    return dict(n_matvec=out8["n_matvec"], n_restarts=out8["n_restarts"], n_resid_matvec=out8["n_resid_matvec"],
+                evals=[float(v) for v in out8["evals"]], oracle_seconds=round(time.time() - t0, 1))
 
 
 if __name__ == "__main__":
