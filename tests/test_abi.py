@@ -129,6 +129,7 @@ def test_null_context_calls(lib):
     assert lib.jtrlan_solve(None, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_pairs(None, 0, None, None, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_apply(None, None, None) == B.JTRLAN_EINVAL
+    assert lib.jtrlan_apply_filter(None, None, None) == B.JTRLAN_EINVAL
     assert lib.jtrlan_get_profile(None, None) == B.JTRLAN_EINVAL
     lib.jtrlan_destroy(None)
 
