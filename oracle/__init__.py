@@ -12,6 +12,9 @@ Contents:
   trlan_jsym  -- Algorithm 1 (TRLAN-JSYM) and Algorithm 2 (LANCZOS_JSYM) in FP64,
                  in the paper's order and notation.
   jacobi      -- the cyclic Jacobi eigensolver that diagonalises T_m in Algorithm 1.
+  inertia     -- eigenvalue counts below a shift by Sylvester's law of inertia (LDL^H), which
+                 check that Algorithm 1's nev pairs are the nev smallest.
+  cg          -- conjugate gradients for the invert mode's products A^{-1} v.
   filter      -- polynomial filters p(A) (Chebyshev recurrence, damped step coefficients);
                  the paper has none, these are standard definitions.
   mlp         -- the 3-layer perceptron that predicts filter coefficients: forward pass,
