@@ -107,6 +107,26 @@ def test_certifying_filter_product_matches_oracle(dims, links, degree, precision
     s.close()
 
 
+@pytest.mark.parametrize("precision", ["mixed_reorth", "fp64"])
+def test_certifying_filter_product_on_a_dense_operator(precision):
+    """The dense operator keeps the FP64 product in every form, so p(A) x comes out of FP64 products
+    and FP64 recurrence steps: within 10 d 2^-52 of max|p(A) x|."""
+    A11, A12 = inputs.dense_jsym(100, 5)
+    mv = lambda x: jsym.dense_matvec(A11, A12, x)
+    lam = np.linalg.eigvalsh(jsym.assemble_block_form(A11, A12))
+    win = (lam[0] - 0.5, lam[-1] + 0.5)
+    degree = 40
+    g = np.random.default_rng(7).standard_normal(degree + 1) / np.sqrt(degree + 1)
+    s = _solver(kind="dense", A11=A11, A12=A12, nev=4, m=16, mwin=8, tol=1e-8, precision=precision,
+                filter_final_coeffs=g, filter_window=win)
+    x = inputs.random_vector(200, 12)
+    y = s.apply_filter(torch.from_numpy(x))
+    assert y.dtype == torch.complex128
+    ref = flt.apply_poly(mv, x, g, *win)
+    assert np.abs(y.cpu().numpy() - ref).max() < 10 * degree * 2.0 ** -52 * np.abs(ref).max()
+    s.close()
+
+
 # ----------------------------------------------------------------------------- filtered solve
 @pytest.mark.parametrize("kind", ["dense", "stencil"])
 def test_filtered_solve_matches_unfiltered_oracle(kind):
