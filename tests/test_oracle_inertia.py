@@ -44,6 +44,23 @@ def test_count_below_with_two_by_two_pivots():
         assert inertia.count_below(A, sigma) == int((lam < sigma).sum())
 
 
+def test_a_count_of_the_diagonal_alone_is_caught(monkeypatch):
+    """Planted mistake: ignoring the 2x2 blocks of D (counting only its diagonal) must fail the pin."""
+    import scipy.linalg
+
+    A = _hermitian(60, 9)
+    A[np.diag_indices_from(A)] = 0.0
+    lam = np.linalg.eigvalsh(A)
+    real_ldl = scipy.linalg.ldl
+
+    def diagonal_only(*a, **k):
+        lu, d, perm = real_ldl(*a, **k)
+        return lu, np.diag(np.diag(d)), perm
+
+    monkeypatch.setattr(inertia.scipy.linalg, "ldl", diagonal_only)
+    assert any(inertia.count_below(A, s) != int((lam < s).sum()) for s in (0.0, (lam[10] + lam[11]) / 2))
+
+
 def test_count_is_even_for_a_jsymmetric_matrix():
     A11, A12 = inputs.dense_jsym(40, 3)
     A = jsym.assemble_block_form(A11, A12)
